@@ -9,8 +9,10 @@
  *
  * With a mate array, (b) is the symmetry rule mate[mate[v]] == v: a vertex
  * can name only one partner, so a symmetric mate array is a set of disjoint
- * pairs.  Each named partner must also be a neighbour (the output edge must
- * exist in the graph), and (a) is checked over every stored CSR entry.
+ * pairs.  Each named partner must also be a neighbour: the output edge must
+ * exist in the graph, stored in the row of either endpoint (Section V-C lets
+ * a CSR hold an edge for one endpoint only).  (a) is checked over every stored
+ * CSR entry.
  *
  * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may
  * call this file.  It shares no code with the CUDA library.
@@ -20,7 +22,7 @@
  *     m >= n or m == v           -> n_bad_range, v is a bad vertex
  *     else n_matched += 1, and
  *       mate[m] != v             -> n_asym,      v is a bad vertex
- *       m not among N_v          -> n_nonedge,   v is a bad vertex
+ *       m not in row v and v not in row m -> n_nonedge, v is a bad vertex
  *   n_pairs = #{v : m = mate[v] in range, v < m, mate[m] == v}
  *   for every entry i of row x with y = nbrs[i], y != x:
  *     mate[x] == NONE and mate[y] == NONE -> n_uncovered (first = min i)
@@ -85,7 +87,10 @@ int oracle_check(uint64_t n, const int64_t *offsets, const uint32_t *nbrs,
             r.n_matched++;
             if ((uint64_t)mate[m] != v) { r.n_asym++; bad = 1; }
             else if (v < m) r.n_pairs++;
-            if (!row_contains(offsets, nbrs, v, m)) { r.n_nonedge++; bad = 1; }
+            if (!row_contains(offsets, nbrs, v, m) && !row_contains(offsets, nbrs, m, v)) {
+                r.n_nonedge++;
+                bad = 1;
+            }
         }
         if (bad && v < r.first_bad_vertex) r.first_bad_vertex = v;
     }

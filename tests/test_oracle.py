@@ -181,6 +181,23 @@ def test_checker_accepts_exactly_the_maximal_matchings(n):
             assert (v.flags == 0) == ok, (adj, mate, v.as_dict())
 
 
+@pytest.mark.parametrize("n", [3, 4])
+def test_checker_on_edges_stored_once(n):
+    """Each edge kept only in the row of its lower end (Section V-C): the checker
+    still accepts exactly the maximal matchings of the edge set."""
+    import itertools
+    vals = [NONE] + list(range(n))
+    for adj in brute.graphs_on(n):
+        once = [[y for y in adj[x] if y > x] for x in range(n)]
+        off, nb = brute.csr_from_adj(n, once)
+        for mate in itertools.product(vals, repeat=n):
+            ok = brute.mate_is_valid_maximal(n, off, nb, list(mate))
+            v = oracle.check(off, nb, np.array(mate, dtype=np.uint32))
+            assert (v.flags == 0) == ok, (once, mate, v.as_dict())
+        m, p = oracle.sgmm(off, nb)
+        assert brute.mate_is_valid_maximal(n, off, nb, m.tolist())
+
+
 def test_every_maximal_matching_within_half_of_maximum():
     rng = random.Random(3)
     for _ in range(60):
