@@ -1,0 +1,248 @@
+/*
+ * skipper.h -- C ABI of libskipper, Skipper maximal matching on one GB300.
+ *
+ * Skipper (Koohi Esfahani, "Skipper: Asynchronous Maximal Matching with a
+ * Single Pass over Edges") resolves every edge of an undirected graph once,
+ * by a just-in-time reservation on a per-vertex state that runs
+ * ACC -> RSVD -> MCHD (Section IV-B, Fig. 4; Algorithm 1).  The result is a
+ * maximal matching: no two output edges share an endpoint and every edge
+ * touches an output edge (Section II-B).
+ *
+ * Graph input (Section II-A, the CSR definition N_v = neighbors[offsets[v] ..
+ * offsets[v+1])): a CSR with n vertices and nnz stored entries,
+ *   offsets  int64_t[n+1] in device memory, offsets[0] = 0, non-decreasing,
+ *            offsets[n] = nnz;
+ *   nbrs     uint32_t[nnz] in device memory, every id < n, base address
+ *            16-byte aligned (the sweep reads it with 128-bit loads).
+ * The library reads each stored entry (x, nbrs[i]) as the edge {x, nbrs[i]};
+ * a graph stored once per direction (symmetric CSR) is the usual input, and
+ * an edge stored for one endpoint only is matched all the same (Section V-C,
+ * "Input Format & Symmetrization").  Self-loops are ignored (Algorithm 1
+ * skips them).  Vertex ids are uint32 with n <= 0xFFFFFFFD.
+ *
+ * Output: mate uint32_t[n] in device memory, mate[v] = the vertex matched to
+ * v, or MM_UNMATCHED.  Optionally the matched pairs (u, mate[u]) with
+ * u < mate[u], in ascending u, as uint32_t[2*count].
+ *
+ * Ownership: the caller owns the CSR arrays and every output buffer; a
+ * mm_graph handle only borrows the CSR, which must outlive it.  The handle
+ * owns its scratch (state array, partition table, control words).
+ *
+ * Streams and errors: every call takes a CUDA stream (cudaStream_t passed as
+ * void*, NULL = the legacy default stream) and is ordered on it.  Calls return
+ * a status code and never throw; mm_last_error() gives a message for the last
+ * failing call on the calling thread.  There is no CPU fallback: without a
+ * CUDA device calls return MM_ERR_CUDA.
+ */
+#ifndef SKIPPER_H
+#define SKIPPER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MM_UNMATCHED 0xFFFFFFFFu
+#define MM_MAX_VERTICES 0xFFFFFFFDull
+
+typedef enum mm_status {
+    MM_OK = 0,
+    MM_ERR_ARG = 1,          /* null pointer, bad size, bad alignment, bad option */
+    MM_ERR_OOM = 2,          /* device memory for the handle's scratch could not be had */
+    MM_ERR_CUDA = 3,         /* a CUDA call failed (includes: no device) */
+    MM_ERR_TIMEOUT = 4,      /* a wait on a reserved vertex exceeded spin_limit polls */
+    MM_ERR_BAD_GRAPH = 5,    /* CSR check failed, or a neighbour id >= n was met */
+    MM_ERR_UNSUPPORTED = 6   /* option combination not supported */
+} mm_status;
+
+/* mm_create_csr flags */
+#define MM_CHECK_CSR 1u      /* check offsets and ids on the device (synchronous) */
+
+typedef struct mm_graph mm_graph;
+
+/*
+ * Options of one matching call.  mm_default_options() fills the defaults;
+ * zero in a field also selects its default.
+ */
+typedef struct mm_options {
+    uint32_t status_bits;    /* 8: one state byte per vertex, 4 packed in a word
+                                (the paper's one byte per vertex, Section IV-C);
+                                32: one word per vertex that is also the mate
+                                entry (ACC = MM_UNMATCHED, RSVD = 0xFFFFFFFE,
+                                matched = partner id).  0 = 8. */
+    uint32_t serial;         /* 1: one GPU thread walks rows in ascending order and
+                                neighbours in stored order (per graph in batched
+                                mode); the result equals sequential greedy MM. */
+    uint32_t grain;          /* merge-path items (rows + entries) per work unit;
+                                0 = 2048.  Must be a multiple of 128 when set. */
+    uint32_t block_threads;  /* sweep threads per block, multiple of 32, <= 512;
+                                0 = 512 */
+    uint32_t blocks_per_sm;  /* sweep blocks per SM; 0 = the occupancy maximum */
+    uint32_t nosync;         /* 1: return without waiting for the GPU; the status
+                                of the work (timeout, bad id) is read by mm_sync() */
+    uint32_t timing;         /* 1: record CUDA events around each kernel on the
+                                call's stream (no extra wait); read back with
+                                mm_get_timing() / mm_timing_history() */
+    uint32_t use_graph;      /* mm_skipper_batched: 1 = launch through a CUDA graph
+                                captured once per handle and option set */
+    uint32_t l2_persist;     /* 1: L2 access-policy window (persisting) over the
+                                state array for the sweep; 0 = per-load hints only */
+    uint32_t reserved0;
+    uint64_t spin_limit;     /* polls of one wait before the call fails with
+                                MM_ERR_TIMEOUT; 0 = 1 << 20 */
+    uint64_t poison_vertex;  /* fault injection for tests: v + 1 leaves vertex v
+                                RESERVED by no thread after initialisation, so
+                                every wait on it runs out; 0 = off */
+    uint64_t reserved[4];
+} mm_options;
+
+/* Per-kernel device times of the last call made with options.timing = 1. */
+typedef struct mm_timing {
+    float init_ms;           /* state initialisation + merge-path partition */
+    float sweep_ms;          /* the single pass over the entries (Algorithm 1) */
+    float compact_ms;        /* pair-list compaction (0 when not requested) */
+    float total_ms;          /* first event to last event */
+    uint64_t units;          /* merge-path work units of the sweep */
+    uint64_t reserved[3];
+} mm_timing;
+
+/*
+ * Verdict of mm_validate (the exact checker, Section II-B).  flags == 0 means
+ * mate is a maximal matching of the graph and the pair list (when given)
+ * lists exactly its pairs.  Counting rules:
+ *   for every v with m = mate[v] != MM_UNMATCHED:
+ *     m >= n or m == v     -> n_bad_range, v is a bad vertex
+ *     otherwise n_matched += 1, and
+ *       mate[m] != v       -> n_asym,    v is a bad vertex
+ *       m is not in row v and v is not in row m -> n_nonedge, v is a bad vertex
+ *   n_pairs = #{v : m = mate[v] in range, v < m, mate[m] == v}
+ *   each entry i of row x with y = nbrs[i] != x, mate[x] and mate[y] both
+ *     MM_UNMATCHED -> n_uncovered (first_uncovered = smallest such i)
+ *   pair list: (a, b) is valid when a < b < n, mate[a] == b, mate[b] == a;
+ *     n_pairs_bad = invalid pairs + repeats of valid pairs; MM_V_PAIRS is set
+ *     when n_pairs_bad > 0 or count != n_pairs.
+ * first_bad_vertex / first_uncovered are UINT64_MAX when there is none.
+ */
+#define MM_V_RANGE     1u
+#define MM_V_ASYM      2u
+#define MM_V_NONEDGE   4u
+#define MM_V_UNCOVERED 8u
+#define MM_V_PAIRS     16u
+
+typedef struct mm_verdict {
+    uint32_t flags;
+    uint32_t pad;
+    uint64_t n_matched;
+    uint64_t n_pairs;
+    uint64_t n_bad_range;
+    uint64_t n_asym;
+    uint64_t n_nonedge;
+    uint64_t n_uncovered;
+    uint64_t n_pairs_bad;
+    uint64_t first_bad_vertex;
+    uint64_t first_uncovered;
+} mm_verdict;
+
+/* Library version string, e.g. "skipper-gb300 0.1 sm_103a". */
+const char *mm_version(void);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *mm_last_error(void);
+
+/* Fill *o with the defaults.  Returns MM_ERR_ARG when o is NULL. */
+mm_status mm_default_options(mm_options *o);
+
+/*
+ * Create a handle over a device CSR (Section II-A).  Borrows d_offsets
+ * (int64_t[n+1]) and d_nbrs (uint32_t[nnz], 16-byte aligned); allocates the
+ * state array (ceil(n/4) words), the merge-path partition table and control
+ * words on the current device.  With MM_CHECK_CSR the CSR is checked on the
+ * device before returning (offsets[0] = 0, non-decreasing, offsets[n] = nnz,
+ * every id < n) and MM_ERR_BAD_GRAPH is returned on failure.
+ * Errors: MM_ERR_ARG (null out, n > MM_MAX_VERTICES, null arrays with n or
+ * nnz > 0, misaligned d_nbrs), MM_ERR_OOM, MM_ERR_CUDA, MM_ERR_BAD_GRAPH.
+ */
+mm_status mm_create_csr(uint64_t n, uint64_t nnz, const int64_t *d_offsets,
+                        const uint32_t *d_nbrs, uint32_t flags, void *cuda_stream,
+                        mm_graph **out);
+
+/*
+ * Skipper's single pass (Algorithm 1): every vertex starts ACC (lines 3-4);
+ * every stored entry (x, y), x != y, is resolved once with u = min(x, y),
+ * v = max(x, y): reserve u ACC->RSVD, claim v ACC->MCHD, then set u MCHD or
+ * release it to ACC (lines 5-18).  Entries are split into equal merge-path
+ * units over rows and entries (the GPU form of the paper's equal-edge blocks,
+ * Section IV-C); once the row vertex x is MCHD the rest of row x is not read.
+ *
+ *   d_mate   uint32_t[n], caller-owned, written in full.
+ *   d_pairs  uint32_t[2*cap] or NULL: pairs (u, mate[u]), u < mate[u], ascending u.
+ *   d_count  uint64_t[1] or NULL: number of pairs (written when d_pairs or
+ *            d_count is given; pairs beyond cap are counted, not written).
+ * Waits for the GPU unless o->nosync; returns MM_ERR_TIMEOUT when a wait ran
+ * past o->spin_limit, MM_ERR_BAD_GRAPH when an id >= n was met.  The result
+ * is a maximal matching; which one depends on timing (Section V-C), except in
+ * serial mode, where it is the sequential greedy result.
+ */
+mm_status mm_skipper(mm_graph *g, const mm_options *o, uint32_t *d_mate, uint32_t *d_pairs,
+                     uint64_t cap, uint64_t *d_count, void *cuda_stream);
+
+/*
+ * Batched Skipper over num_graphs graphs packed block-diagonally in the
+ * handle's CSR with global ids: graph k owns vertices [vbase[k], vbase[k+1])
+ * and entries [ebase[k], ebase[k+1]), and no entry leaves its block.  One
+ * persistent sweep covers all graphs (Skipper on the union is Skipper on each
+ * block, since no edge crosses blocks).  d_vbase, d_ebase: int64_t[num_graphs+1]
+ * in device memory, vbase[0] = ebase[0] = 0, vbase[num_graphs] = n,
+ * ebase[num_graphs] = nnz.  d_mate: uint32_t[n] (global ids).
+ * d_graph_pairs: uint64_t[num_graphs] or NULL, matched pairs per graph.
+ * With o->serial each graph is walked by one thread in SGMM order (so the
+ * result equals sequential greedy MM on every graph).  With o->use_graph the
+ * launches run as a CUDA graph captured once per handle and options, whose
+ * kernel arguments are updated per call.
+ */
+mm_status mm_skipper_batched(mm_graph *g, uint64_t num_graphs, const int64_t *d_vbase,
+                             const int64_t *d_ebase, const mm_options *o, uint32_t *d_mate,
+                             uint64_t *d_graph_pairs, void *cuda_stream);
+
+/*
+ * Exact checker on the device (Section II-B; counting rules above).
+ * d_pairs may be NULL (count ignored).  Synchronous: *h_out is filled before
+ * return.  Errors: MM_ERR_ARG, MM_ERR_CUDA, MM_ERR_OOM.
+ */
+mm_status mm_validate(mm_graph *g, const uint32_t *d_mate, const uint32_t *d_pairs,
+                      uint64_t count, mm_verdict *h_out, void *cuda_stream);
+
+/* Wait for the handle's last call on cuda_stream and return its device status
+ * (MM_OK, MM_ERR_TIMEOUT or MM_ERR_BAD_GRAPH).  Used after nosync calls. */
+mm_status mm_sync(mm_graph *g, void *cuda_stream);
+
+/* Per-kernel times of the last call made with o->timing = 1 (waits for its
+ * events).  MM_ERR_ARG when no timed call was made since the last
+ * mm_timing_history. */
+mm_status mm_get_timing(mm_graph *g, mm_timing *out);
+
+/* Per-kernel times of the latest timed calls (at most 256 are kept), oldest
+ * first: writes min(max, kept) entries to out[], their number to *count, and
+ * clears the history.  Timed calls record CUDA events on their stream and do
+ * not wait for them; this call waits. */
+mm_status mm_timing_history(mm_graph *g, mm_timing *out, uint32_t max, uint32_t *count);
+
+/*
+ * Autotuner for mm_skipper_batched: times the candidate (grain, status_bits,
+ * block_threads) settings on this batch with CUDA events, keeps the fastest
+ * whose result passes the device checker, and writes it into *o (other fields
+ * of *o are kept).  d_mate_scratch: uint32_t[n].  Synchronous.
+ */
+mm_status mm_autotune_batched(mm_graph *g, uint64_t num_graphs, const int64_t *d_vbase,
+                              const int64_t *d_ebase, uint32_t *d_mate_scratch,
+                              mm_options *o, void *cuda_stream);
+
+/* Release the handle's scratch.  Does not touch the borrowed CSR. */
+mm_status mm_destroy(mm_graph *g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SKIPPER_H */

@@ -1,0 +1,242 @@
+"""Skipper maximal matching on GB300 (sm_103a CUDA behind a C ABI).
+
+Skipper (Koohi Esfahani, arXiv 2507.04420) resolves every edge of an
+undirected graph once, with a just-in-time reservation on a per-vertex state
+ACC -> RSVD -> MCHD (Section IV, Algorithm 1).  This package is a thin binding
+over ``libskipper.so`` (``include/skipper.h``): it only marshals torch tensors
+(device memory) and streams into the C calls.  Every step of the matching runs
+in the library's kernels; if the library is missing, import fails.
+
+Mate arrays are returned as ``torch.int32`` tensors that hold uint32 bits:
+an unmatched vertex reads as -1 (0xFFFFFFFF).
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import torch
+
+from . import _native
+from ._native import Options, Timing, Verdict
+
+__all__ = ["Graph", "HostSession", "SkipperError", "match", "validate", "Options", "Verdict", "Timing",
+           "UNMATCHED", "lib", "options"]
+
+UNMATCHED = 0xFFFFFFFF
+V_RANGE, V_ASYM, V_NONEDGE, V_UNCOVERED, V_PAIRS = 1, 2, 4, 8, 16
+
+lib = _native.load()
+
+
+class SkipperError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = lib.mm_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {_native.STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.status = _native.STATUS.get(code, str(code))
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise SkipperError(code, where)
+
+
+def options(**kw) -> Options:
+    """mm_options with the library defaults, overridden by keyword fields."""
+    o = Options()
+    _check(lib.mm_default_options(ctypes.byref(o)), "mm_default_options")
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k!r}")
+        setattr(o, k, int(v))
+    return o
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[ctypes.c_void_p]:
+    return None if t is None else ctypes.c_void_p(int(t.data_ptr()))
+
+
+def _need(t: torch.Tensor, name: str, dtypes):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be in CUDA device memory")
+    if t.dtype not in dtypes:
+        raise TypeError(f"{name} must have dtype in {dtypes}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+_U32 = tuple(d for d in (torch.int32, getattr(torch, "uint32", None)) if d is not None)
+
+
+class Graph:
+    """A device CSR handle (mm_create_csr); borrows offsets/nbrs, which must outlive it."""
+
+    def __init__(self, offsets: torch.Tensor, nbrs: torch.Tensor, check: bool = True, stream=None):
+        _need(offsets, "offsets", (torch.int64,))
+        _need(nbrs, "nbrs", _U32)
+        self.offsets, self.nbrs = offsets, nbrs
+        self.n = offsets.numel() - 1
+        self.nnz = nbrs.numel()
+        h = ctypes.c_void_p()
+        _check(lib.mm_create_csr(self.n, self.nnz, _ptr(offsets), _ptr(nbrs) if self.nnz else None,
+                                 1 if check else 0, _stream_ptr(stream), ctypes.byref(h)),
+               "mm_create_csr")
+        self._h = h
+
+    # -- matching -------------------------------------------------------------
+    def skipper(self, mate: Optional[torch.Tensor] = None, pairs: bool = False,
+                cap: Optional[int] = None, stream=None, opts: Optional[Options] = None, **kw):
+        """Run Skipper; returns mate (int32 view of uint32), plus (pairs, count) if asked."""
+        o = opts if opts is not None else options(**kw)
+        dev = self.offsets.device
+        if mate is None:
+            mate = torch.empty(self.n, dtype=torch.int32, device=dev)
+        _need(mate, "mate", _U32)
+        if mate.numel() != self.n:
+            raise ValueError("mate must have n entries")
+        d_pairs = d_count = None
+        if pairs:
+            cap = cap if cap is not None else max(self.n // 2, 1)
+            d_pairs = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+            d_count = torch.zeros(1, dtype=torch.int64, device=dev)
+        _check(lib.mm_skipper(self._h, ctypes.byref(o), _ptr(mate), _ptr(d_pairs),
+                              cap if pairs else 0, _ptr(d_count), _stream_ptr(stream)),
+               "mm_skipper")
+        if pairs:
+            return mate, d_pairs, d_count
+        return mate
+
+    def batched(self, vbase: torch.Tensor, ebase: torch.Tensor, mate: Optional[torch.Tensor] = None,
+                graph_pairs: bool = False, stream=None, opts: Optional[Options] = None, **kw):
+        """Batched Skipper over a block-diagonal packing (vbase/ebase int64[G+1] on device)."""
+        _need(vbase, "vbase", (torch.int64,))
+        _need(ebase, "ebase", (torch.int64,))
+        o = opts if opts is not None else options(**kw)
+        G = vbase.numel() - 1
+        if mate is None:
+            mate = torch.empty(self.n, dtype=torch.int32, device=self.offsets.device)
+        _need(mate, "mate", _U32)
+        gp = torch.empty(G, dtype=torch.int64, device=self.offsets.device) if graph_pairs else None
+        _check(lib.mm_skipper_batched(self._h, G, _ptr(vbase), _ptr(ebase), ctypes.byref(o),
+                                      _ptr(mate), _ptr(gp), _stream_ptr(stream)),
+               "mm_skipper_batched")
+        return (mate, gp) if graph_pairs else mate
+
+    def autotune_batched(self, vbase: torch.Tensor, ebase: torch.Tensor, stream=None,
+                         opts: Optional[Options] = None, **kw) -> Options:
+        o = opts if opts is not None else options(**kw)
+        scratch = torch.empty(self.n, dtype=torch.int32, device=self.offsets.device)
+        _check(lib.mm_autotune_batched(self._h, vbase.numel() - 1, _ptr(vbase), _ptr(ebase),
+                                       _ptr(scratch), ctypes.byref(o), _stream_ptr(stream)),
+               "mm_autotune_batched")
+        return o
+
+    def sync(self, stream=None):
+        _check(lib.mm_sync(self._h, _stream_ptr(stream)), "mm_sync")
+
+    def validate(self, mate: torch.Tensor, pairs: Optional[torch.Tensor] = None,
+                 count: Optional[int] = None, stream=None) -> Verdict:
+        _need(mate, "mate", _U32)
+        if pairs is not None:
+            _need(pairs, "pairs", _U32)
+            count = pairs.shape[0] if count is None else count
+        v = Verdict()
+        _check(lib.mm_validate(self._h, _ptr(mate), _ptr(pairs), count or 0, ctypes.byref(v),
+                               _stream_ptr(stream)), "mm_validate")
+        return v
+
+    @staticmethod
+    def _tdict(t) -> dict:
+        return {"init_ms": t.init_ms, "sweep_ms": t.sweep_ms, "compact_ms": t.compact_ms,
+                "total_ms": t.total_ms, "units": int(t.units)}
+
+    def timing(self) -> dict:
+        """Per-kernel times of the last call made with timing=1."""
+        t = Timing()
+        _check(lib.mm_get_timing(self._h, ctypes.byref(t)), "mm_get_timing")
+        return self._tdict(t)
+
+    def timing_history(self, max_calls: int = 256) -> list:
+        """Per-kernel times of the latest timed calls (oldest first); clears them."""
+        arr = (Timing * max_calls)()
+        cnt = ctypes.c_uint32(0)
+        _check(lib.mm_timing_history(self._h, arr, max_calls, ctypes.byref(cnt)),
+               "mm_timing_history")
+        return [self._tdict(arr[i]) for i in range(cnt.value)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.mm_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def match(offsets: torch.Tensor, nbrs: torch.Tensor, **kw) -> torch.Tensor:
+    """One-shot Skipper on a device CSR; returns the mate array (int32 view of uint32)."""
+    with Graph(offsets, nbrs) as g:
+        return g.skipper(**kw)
+
+
+def validate(offsets: torch.Tensor, nbrs: torch.Tensor, mate: torch.Tensor, pairs=None) -> Verdict:
+    with Graph(offsets, nbrs, check=False) as g:
+        return g.validate(mate, pairs)
+
+
+class HostSession:
+    """Skipper on graphs that live in host memory.
+
+    Keeps device buffers for up to (n_max, nnz_max) and one library handle;
+    each run() copies the CSR host->device, matches, and copies the mate
+    array back (pinned host tensors give asynchronous copies)."""
+
+    def __init__(self, n_max: int, nnz_max: int, device=None):
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.n_max, self.nnz_max = n_max, nnz_max
+        self.d_off = torch.zeros(n_max + 1, dtype=torch.int64, device=dev)
+        self.d_nb = torch.empty(max(nnz_max, 4), dtype=torch.int32, device=dev)
+        self.d_mate = torch.empty(max(n_max, 1), dtype=torch.int32, device=dev)
+        self._graphs = {}
+
+    def run(self, offsets: torch.Tensor, nbrs: torch.Tensor, mate_out: Optional[torch.Tensor] = None,
+            stream=None, **kw) -> torch.Tensor:
+        n, nnz = offsets.numel() - 1, nbrs.numel()
+        if n > self.n_max or nnz > self.nnz_max:
+            raise ValueError("graph larger than the session's buffers")
+        off_d, nb_d, mate_d = self.d_off[: n + 1], self.d_nb[:nnz], self.d_mate[:n]
+        off_d.copy_(offsets, non_blocking=True)
+        nb_d.copy_(nbrs, non_blocking=True)
+        key = (n, nnz)
+        g = self._graphs.get(key)
+        if g is None:  # the handle only borrows the buffers; their contents change per run
+            g = self._graphs[key] = Graph(off_d, nb_d, check=False, stream=stream)
+        g.skipper(mate=mate_d, stream=stream, **kw)
+        if mate_out is None:
+            mate_out = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        mate_out.copy_(mate_d, non_blocking=True)
+        (stream or torch.cuda.current_stream()).synchronize()
+        return mate_out
+
+    def close(self):
+        for g in self._graphs.values():
+            g.close()
+        self._graphs.clear()

@@ -1,0 +1,670 @@
+// api.cu -- the C ABI of libskipper (declared in include/skipper.h).
+//
+// Host side only: argument checks, scratch ownership, kernel launches on the
+// caller's stream, the batched CUDA graph, the autotuner and error reporting.
+// Every step of the matching itself runs in the kernels of sweep.cu and
+// check.cu; there is no host fallback.
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "skipper.h"
+
+using namespace skp;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+mm_status fail(mm_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+#define CUDA_TRY(expr)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail(e_ == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA, "%s: %s (%s)", \
+                  #expr, cudaGetErrorString(e_), __func__);                                  \
+  } while (0)
+
+constexpr uint32_t kDefaultGrain = 2048;
+constexpr int kDefaultBlock = 512;
+constexpr uint64_t kDefaultSpin = 1ull << 20;
+
+struct BatchGraph {
+  bool valid = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t n_prepare = nullptr, n_sweep = nullptr, n_pairs = nullptr, n_copy = nullptr;
+  // signature of the options the graph was built for
+  uint32_t status_bits = 0, serial = 0, grain = 0, block = 0, blocks_per_sm = 0;
+  bool with_pairs = false;
+  uint64_t num_graphs = 0;
+};
+
+}  // namespace
+
+struct mm_graph {
+  int device = 0;
+  int num_sms = 0;
+  uint64_t n = 0, nnz = 0;
+  const int64_t* offsets = nullptr;
+  const uint32_t* nbrs = nullptr;
+  uint32_t* state = nullptr;          // ceil(n/4) words (+ slack)
+  int64_t* part = nullptr;
+  uint64_t part_units_cap = 0;
+  unsigned long long* ctrl = nullptr;  // [0] work counter, [1] err word, [2] csr-check count,
+                                       // [8..16] checker counters
+  uint32_t* seen_bits = nullptr;
+  uint64_t* tile_counts = nullptr;
+  uint64_t tile_cap = 0;
+  uint32_t* h_err = nullptr;           // pinned
+  unsigned long long* h_counters = nullptr;  // pinned, 16 words
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // event sets of timed calls, read back without blocking the calls themselves
+  static constexpr uint32_t kHist = 256;
+  cudaEvent_t hist[kHist][4] = {};
+  uint64_t hist_units[kHist] = {};
+  bool hist_compact[kHist] = {};
+  uint64_t hist_count = 0;   // timed calls since the last mm_timing_history
+  bool hist_ready = false;
+  mm_timing timing{};
+  BatchGraph bg;
+};
+
+namespace {
+
+unsigned long long* work_ptr(mm_graph* g) { return g->ctrl; }
+uint32_t* err_ptr(mm_graph* g) { return reinterpret_cast<uint32_t*>(g->ctrl + 1); }
+unsigned long long* csr_bad_ptr(mm_graph* g) { return g->ctrl + 2; }
+unsigned long long* counters_ptr(mm_graph* g) { return g->ctrl + 8; }
+
+struct Resolved {
+  bool word;
+  bool serial;
+  uint32_t grain;
+  int block;
+  int blocks_per_sm;
+  bool nosync, timing, use_graph, l2_persist;
+  uint64_t spin_limit, poison;
+};
+
+mm_status resolve(const mm_graph* g, const mm_options* o, Resolved* r) {
+  mm_options d;
+  mm_default_options(&d);
+  if (!o) o = &d;
+  const uint32_t bits = o->status_bits ? o->status_bits : 8u;
+  if (bits != 8 && bits != 32) return fail(MM_ERR_ARG, "status_bits must be 8 or 32 (got %u)", bits);
+  r->word = bits == 32;
+  r->serial = o->serial != 0;
+  r->grain = o->grain ? o->grain : kDefaultGrain;
+  if (r->grain % 128 || r->grain > (1u << 24))
+    return fail(MM_ERR_ARG, "grain must be a multiple of 128 and at most 2^24 (got %u)", r->grain);
+  r->block = o->block_threads ? (int)o->block_threads : kDefaultBlock;
+  if (r->block < 32 || r->block > 512 || r->block % 32)
+    return fail(MM_ERR_ARG, "block_threads must be a multiple of 32 in [32, 512] (got %d)", r->block);
+  r->blocks_per_sm = (int)o->blocks_per_sm;
+  r->nosync = o->nosync != 0;
+  r->timing = o->timing != 0;
+  r->use_graph = o->use_graph != 0;
+  r->l2_persist = o->l2_persist != 0;
+  r->spin_limit = o->spin_limit ? o->spin_limit : kDefaultSpin;
+  r->poison = o->poison_vertex;
+  if (r->poison > g->n) return fail(MM_ERR_ARG, "poison_vertex out of range");
+  if (r->word && g->n > MM_MAX_VERTICES) return fail(MM_ERR_ARG, "n too large for 32-bit states");
+  return MM_OK;
+}
+
+mm_status ensure_part(mm_graph* g, uint64_t units) {
+  if (units <= g->part_units_cap && g->part) return MM_OK;
+  if (g->part) cudaFree(g->part);
+  g->part = nullptr;
+  g->part_units_cap = 0;
+  CUDA_TRY(cudaMalloc(&g->part, (units + 1) * 2 * sizeof(int64_t)));
+  g->part_units_cap = units;
+  return MM_OK;
+}
+
+int sweep_grid(const mm_graph* g, const Resolved& r) {
+  const int per_sm = r.blocks_per_sm > 0 ? r.blocks_per_sm : sweep_blocks_per_sm(r.word, r.block);
+  return g->num_sms * per_sm;
+}
+
+int prepare_grid(const mm_graph* g) { return g->num_sms * 8; }
+
+SweepParams make_params(mm_graph* g, const Resolved& r, uint32_t* d_mate) {
+  SweepParams P{};
+  P.n = g->n;
+  P.nnz = g->nnz;
+  P.offsets = g->offsets;
+  P.nbrs = g->nbrs;
+  P.mate = d_mate;
+  P.state = r.word ? d_mate : g->state;
+  P.grain = r.grain;
+  P.units = (g->n + g->nnz + r.grain - 1) / r.grain;
+  P.part = g->part;
+  P.work = work_ptr(g);
+  P.err = err_ptr(g);
+  P.spin_limit = r.spin_limit;
+  P.poison = r.poison;
+  return P;
+}
+
+mm_status read_err(mm_graph* g, cudaStream_t s) {
+  CUDA_TRY(cudaStreamSynchronize(s));
+  const uint32_t e = *g->h_err;
+  if (e & kErrTimeout) return fail(MM_ERR_TIMEOUT, "a wait on a reserved vertex ran past spin_limit");
+  if (e & kErrBadId) return fail(MM_ERR_BAD_GRAPH, "a neighbour id >= n was met");
+  return MM_OK;
+}
+
+// L2 persisting window over the state array for the sweep (opt-in); the
+// stream attribute and the context's set-aside are put back afterwards.
+struct L2Window {
+  bool on = false;
+  cudaStream_t s{};
+  size_t old_limit = 0;
+  mm_status open(mm_graph* g, const Resolved& r, cudaStream_t st, const uint32_t* base, size_t bytes) {
+    if (!r.l2_persist) return MM_OK;
+    int max_win = 0, max_persist = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, g->device));
+    CUDA_TRY(cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, g->device));
+    if (max_win <= 0 || max_persist <= 0) return MM_OK;
+    CUDA_TRY(cudaDeviceGetLimit(&old_limit, cudaLimitPersistingL2CacheSize));
+    const size_t want = bytes < (size_t)max_persist ? bytes : (size_t)max_persist;
+    CUDA_TRY(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want));
+    cudaStreamAttrValue a{};
+    a.accessPolicyWindow.base_ptr = const_cast<uint32_t*>(base);
+    a.accessPolicyWindow.num_bytes = bytes < (size_t)max_win ? bytes : (size_t)max_win;
+    a.accessPolicyWindow.hitRatio = a.accessPolicyWindow.num_bytes > want
+                                        ? (float)want / (float)a.accessPolicyWindow.num_bytes
+                                        : 1.0f;
+    a.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    a.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    CUDA_TRY(cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &a));
+    on = true;
+    s = st;
+    return MM_OK;
+  }
+  mm_status close() {
+    if (!on) return MM_OK;
+    on = false;
+    cudaStreamAttrValue a{};
+    a.accessPolicyWindow.num_bytes = 0;
+    CUDA_TRY(cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &a));
+    CUDA_TRY(cudaCtxResetPersistingL2Cache());
+    CUDA_TRY(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, old_limit));
+    return MM_OK;
+  }
+};
+
+mm_status ensure_hist(mm_graph* g) {
+  if (g->hist_ready) return MM_OK;
+  for (auto& set : g->hist)
+    for (auto& e : set) CUDA_TRY(cudaEventCreate(&e));
+  g->hist_ready = true;
+  return MM_OK;
+}
+
+// events of the next timed call (the ring keeps the latest kHist calls)
+cudaEvent_t* next_hist(mm_graph* g, uint64_t units, bool compact) {
+  const uint32_t slot = (uint32_t)(g->hist_count % mm_graph::kHist);
+  g->hist_units[slot] = units;
+  g->hist_compact[slot] = compact;
+  ++g->hist_count;
+  return g->hist[slot];
+}
+
+mm_status read_slot(mm_graph* g, uint32_t slot, mm_timing* out) {
+  cudaEvent_t* ev = g->hist[slot];
+  CUDA_TRY(cudaEventSynchronize(ev[3]));
+  float a = 0, b = 0, c = 0, t = 0;
+  CUDA_TRY(cudaEventElapsedTime(&a, ev[0], ev[1]));
+  CUDA_TRY(cudaEventElapsedTime(&b, ev[1], ev[2]));
+  CUDA_TRY(cudaEventElapsedTime(&c, ev[2], ev[3]));
+  CUDA_TRY(cudaEventElapsedTime(&t, ev[0], ev[3]));
+  *out = mm_timing{};
+  out->init_ms = a;
+  out->sweep_ms = b;
+  out->compact_ms = g->hist_compact[slot] ? c : 0.0f;
+  out->total_ms = t;
+  out->units = g->hist_units[slot];
+  return MM_OK;
+}
+
+mm_status check_handle(const mm_graph* g) {
+  if (!g) return fail(MM_ERR_ARG, "null handle");
+  int dev = -1;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != g->device) return fail(MM_ERR_ARG, "handle belongs to device %d, current is %d", g->device, dev);
+  return MM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mm_version(void) { return "skipper-gb300 0.1 sm_103a"; }
+
+const char* mm_last_error(void) { return g_err; }
+
+mm_status mm_default_options(mm_options* o) {
+  if (!o) return fail(MM_ERR_ARG, "null options");
+  memset(o, 0, sizeof *o);
+  o->status_bits = 8;
+  o->grain = kDefaultGrain;
+  o->block_threads = kDefaultBlock;
+  o->spin_limit = kDefaultSpin;
+  return MM_OK;
+}
+
+mm_status mm_create_csr(uint64_t n, uint64_t nnz, const int64_t* d_offsets, const uint32_t* d_nbrs,
+                        uint32_t flags, void* cuda_stream, mm_graph** out) {
+  g_err[0] = 0;
+  if (!out) return fail(MM_ERR_ARG, "null out");
+  *out = nullptr;
+  if (n > MM_MAX_VERTICES) return fail(MM_ERR_ARG, "n = %llu exceeds %llu", (unsigned long long)n, MM_MAX_VERTICES);
+  if (!d_offsets) return fail(MM_ERR_ARG, "null offsets");
+  if (nnz && !d_nbrs) return fail(MM_ERR_ARG, "null nbrs with nnz > 0");
+  if (nnz && (reinterpret_cast<uintptr_t>(d_nbrs) & 15u))
+    return fail(MM_ERR_ARG, "nbrs must be 16-byte aligned");
+  if (reinterpret_cast<uintptr_t>(d_offsets) & 7u) return fail(MM_ERR_ARG, "offsets must be 8-byte aligned");
+  if (flags & ~MM_CHECK_CSR) return fail(MM_ERR_ARG, "unknown flags 0x%x", flags);
+  int ndev = 0;
+  CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (ndev <= 0) return fail(MM_ERR_CUDA, "no CUDA device");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+
+  mm_graph* g = new (std::nothrow) mm_graph();
+  if (!g) return fail(MM_ERR_OOM, "host allocation failed");
+  mm_status st = MM_OK;
+  auto bail = [&](mm_status code) {
+    mm_destroy(g);
+    return code;
+  };
+#define CREATE_TRY(expr)                                                                   \
+  do {                                                                                     \
+    cudaError_t e_ = (expr);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return bail(fail(e_ == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA, "%s: %s", \
+                       #expr, cudaGetErrorString(e_)));                                    \
+  } while (0)
+  CREATE_TRY(cudaGetDevice(&g->device));
+  CREATE_TRY(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device));
+  g->n = n;
+  g->nnz = nnz;
+  g->offsets = d_offsets;
+  g->nbrs = d_nbrs;
+  const uint64_t words = (n + 3) / 4 + 4;
+  CREATE_TRY(cudaMalloc(&g->state, words * sizeof(uint32_t)));
+  CREATE_TRY(cudaMalloc(&g->ctrl, 32 * sizeof(unsigned long long)));
+  CREATE_TRY(cudaMemsetAsync(g->ctrl, 0, 32 * sizeof(unsigned long long), s));
+  g->tile_cap = (n + kCompactTile - 1) / kCompactTile + 1;
+  CREATE_TRY(cudaMalloc(&g->tile_counts, g->tile_cap * sizeof(uint64_t)));
+  CREATE_TRY(cudaMallocHost(&g->h_err, 64));
+  CREATE_TRY(cudaMallocHost(&g->h_counters, 16 * sizeof(unsigned long long)));
+  *g->h_err = 0;
+  for (auto& e : g->ev) CREATE_TRY(cudaEventCreate(&e));
+  st = ensure_part(g, (n + nnz + kDefaultGrain - 1) / kDefaultGrain);
+  if (st != MM_OK) return bail(st);
+
+  if (flags & MM_CHECK_CSR) {
+    CREATE_TRY(launch_csr_check(n, nnz, d_offsets, d_nbrs, csr_bad_ptr(g), prepare_grid(g), s));
+    CREATE_TRY(cudaMemcpyAsync(g->h_counters, csr_bad_ptr(g), sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, s));
+    CREATE_TRY(cudaStreamSynchronize(s));
+    if (g->h_counters[0] != 0)
+      return bail(fail(MM_ERR_BAD_GRAPH, "CSR check failed: %llu violations (offsets[0] = 0, "
+                       "non-decreasing, offsets[n] = nnz, ids < n)", g->h_counters[0]));
+  }
+#undef CREATE_TRY
+  *out = g;
+  return MM_OK;
+}
+
+mm_status mm_skipper(mm_graph* g, const mm_options* o, uint32_t* d_mate, uint32_t* d_pairs,
+                     uint64_t cap, uint64_t* d_count, void* cuda_stream) {
+  g_err[0] = 0;
+  mm_status st = check_handle(g);
+  if (st != MM_OK) return st;
+  if (!d_mate && g->n) return fail(MM_ERR_ARG, "null mate");
+  if (d_pairs && !cap) return fail(MM_ERR_ARG, "pairs given with cap = 0");
+  Resolved r;
+  if ((st = resolve(g, o, &r)) != MM_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const uint64_t units = (g->n + g->nnz + r.grain - 1) / r.grain;
+  if ((st = ensure_part(g, units)) != MM_OK) return st;
+  const SweepParams P = make_params(g, r, d_mate);
+
+  CheckScratch cs{counters_ptr(g), g->seen_bits, g->tile_counts, g->tile_cap};
+  cudaEvent_t* ev = nullptr;
+  if (r.timing) {
+    if ((st = ensure_hist(g)) != MM_OK) return st;
+    ev = next_hist(g, units, d_pairs || d_count);
+    CUDA_TRY(cudaEventRecord(ev[0], s));
+  }
+  CUDA_TRY(launch_prepare(P, r.word, prepare_grid(g), s, nullptr, 0));
+  if (ev) CUDA_TRY(cudaEventRecord(ev[1], s));
+  L2Window win;
+  if (!r.serial) {
+    if ((st = win.open(g, r, s, P.state, r.word ? g->n * 4 : (g->n + 3) / 4 * 4)) != MM_OK) return st;
+    CUDA_TRY(launch_sweep(P, r.word, sweep_grid(g, r), r.block, s));
+    if ((st = win.close()) != MM_OK) return st;
+  } else {
+    CUDA_TRY(launch_serial(P, r.word, s));
+  }
+  if (ev) CUDA_TRY(cudaEventRecord(ev[2], s));
+  if (d_pairs || d_count) {
+    uint64_t* cnt = d_count;
+    CUDA_TRY(launch_compact(g->n, d_mate, d_pairs, d_pairs ? cap : 0, cnt, cs, s));
+  }
+  if (ev) CUDA_TRY(cudaEventRecord(ev[3], s));
+  CUDA_TRY(cudaMemcpyAsync(g->h_err, err_ptr(g), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  if (r.nosync) return MM_OK;
+  return read_err(g, s);
+}
+
+mm_status mm_sync(mm_graph* g, void* cuda_stream) {
+  g_err[0] = 0;
+  mm_status st = check_handle(g);
+  if (st != MM_OK) return st;
+  return read_err(g, static_cast<cudaStream_t>(cuda_stream));
+}
+
+mm_status mm_get_timing(mm_graph* g, mm_timing* out) {
+  if (!g || !out) return fail(MM_ERR_ARG, "null argument");
+  if (g->hist_count == 0) return fail(MM_ERR_ARG, "no timed call since the last history read");
+  return read_slot(g, (uint32_t)((g->hist_count - 1) % mm_graph::kHist), out);
+}
+
+mm_status mm_timing_history(mm_graph* g, mm_timing* out, uint32_t max, uint32_t* count) {
+  if (!g || !count || (max && !out)) return fail(MM_ERR_ARG, "null argument");
+  const uint64_t have = g->hist_count < mm_graph::kHist ? g->hist_count : mm_graph::kHist;
+  const uint32_t k = (uint32_t)(have < max ? have : max);
+  for (uint32_t i = 0; i < k; ++i) {  // oldest first among the latest k calls
+    const uint64_t call = g->hist_count - k + i;
+    mm_status st = read_slot(g, (uint32_t)(call % mm_graph::kHist), out + i);
+    if (st != MM_OK) return st;
+  }
+  *count = k;
+  g->hist_count = 0;
+  return MM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+mm_status build_batch_graph(mm_graph* g, const Resolved& r, uint64_t num_graphs, bool with_pairs,
+                            const SweepParams& P, uint64_t* graph_pairs) {
+  BatchGraph& b = g->bg;
+  if (b.exec) cudaGraphExecDestroy(b.exec);
+  if (b.graph) cudaGraphDestroy(b.graph);
+  b = BatchGraph{};
+  CUDA_TRY(cudaGraphCreate(&b.graph, 0));
+  const void *k_prepare = nullptr, *k_sweep = nullptr, *k_pairs = nullptr;
+  get_batched_kernels(r.word, r.serial, &k_prepare, &k_sweep, &k_pairs);
+
+  SweepParams p = P;
+  uint64_t* gp = graph_pairs;
+  uint64_t ng = num_graphs;
+  void* prep_args[] = {&p, &gp, &ng};
+  cudaKernelNodeParams kp{};
+  kp.func = const_cast<void*>(k_prepare);
+  kp.gridDim = dim3(prepare_grid(g));
+  kp.blockDim = dim3(256);
+  kp.kernelParams = prep_args;
+  CUDA_TRY(cudaGraphAddKernelNode(&b.n_prepare, b.graph, nullptr, 0, &kp));
+
+  void* sweep_args[] = {&p};
+  cudaKernelNodeParams ks{};
+  ks.func = const_cast<void*>(k_sweep);
+  if (r.serial) {
+    ks.gridDim = dim3((unsigned)((num_graphs + 127) / 128));
+    ks.blockDim = dim3(128);
+  } else {
+    ks.gridDim = dim3(sweep_grid(g, r));
+    ks.blockDim = dim3(r.block);
+  }
+  ks.kernelParams = sweep_args;
+  CUDA_TRY(cudaGraphAddKernelNode(&b.n_sweep, b.graph, &b.n_prepare, 1, &ks));
+  cudaGraphNode_t last = b.n_sweep;
+
+  if (with_pairs) {
+    const uint32_t* mate = P.mate;
+    const int64_t* vb = P.vbase;
+    uint64_t n = g->n;
+    unsigned long long* out = reinterpret_cast<unsigned long long*>(graph_pairs);
+    void* pair_args[] = {&mate, &vb, &ng, &n, &out};
+    cudaKernelNodeParams kq{};
+    kq.func = const_cast<void*>(k_pairs);
+    kq.gridDim = dim3(prepare_grid(g));
+    kq.blockDim = dim3(256);
+    kq.kernelParams = pair_args;
+    CUDA_TRY(cudaGraphAddKernelNode(&b.n_pairs, b.graph, &last, 1, &kq));
+    last = b.n_pairs;
+  }
+  CUDA_TRY(cudaGraphAddMemcpyNode1D(&b.n_copy, b.graph, &last, 1, g->h_err, err_ptr(g),
+                                    sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaGraphInstantiate(&b.exec, b.graph, 0));
+  b.valid = true;
+  b.status_bits = r.word ? 32 : 8;
+  b.serial = r.serial;
+  b.grain = r.grain;
+  b.block = (uint32_t)r.block;
+  b.blocks_per_sm = (uint32_t)r.blocks_per_sm;
+  b.with_pairs = with_pairs;
+  b.num_graphs = num_graphs;
+  return MM_OK;
+}
+
+mm_status update_batch_graph(mm_graph* g, const Resolved& r, uint64_t num_graphs,
+                             const SweepParams& P, uint64_t* graph_pairs) {
+  BatchGraph& b = g->bg;
+  const void *k_prepare = nullptr, *k_sweep = nullptr, *k_pairs = nullptr;
+  get_batched_kernels(r.word, r.serial, &k_prepare, &k_sweep, &k_pairs);
+  SweepParams p = P;
+  uint64_t* gp = graph_pairs;
+  uint64_t ng = num_graphs;
+  void* prep_args[] = {&p, &gp, &ng};
+  cudaKernelNodeParams kp{};
+  CUDA_TRY(cudaGraphKernelNodeGetParams(b.n_prepare, &kp));
+  kp.kernelParams = prep_args;
+  kp.extra = nullptr;
+  CUDA_TRY(cudaGraphExecKernelNodeSetParams(b.exec, b.n_prepare, &kp));
+  void* sweep_args[] = {&p};
+  cudaKernelNodeParams ks{};
+  CUDA_TRY(cudaGraphKernelNodeGetParams(b.n_sweep, &ks));
+  ks.kernelParams = sweep_args;
+  ks.extra = nullptr;
+  CUDA_TRY(cudaGraphExecKernelNodeSetParams(b.exec, b.n_sweep, &ks));
+  if (b.with_pairs) {
+    const uint32_t* mate = P.mate;
+    const int64_t* vb = P.vbase;
+    uint64_t n = g->n;
+    unsigned long long* out = reinterpret_cast<unsigned long long*>(graph_pairs);
+    void* pair_args[] = {&mate, &vb, &ng, &n, &out};
+    cudaKernelNodeParams kq{};
+    CUDA_TRY(cudaGraphKernelNodeGetParams(b.n_pairs, &kq));
+    kq.kernelParams = pair_args;
+    kq.extra = nullptr;
+    CUDA_TRY(cudaGraphExecKernelNodeSetParams(b.exec, b.n_pairs, &kq));
+  }
+  return MM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mm_status mm_skipper_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d_vbase,
+                             const int64_t* d_ebase, const mm_options* o, uint32_t* d_mate,
+                             uint64_t* d_graph_pairs, void* cuda_stream) {
+  g_err[0] = 0;
+  mm_status st = check_handle(g);
+  if (st != MM_OK) return st;
+  if (num_graphs == 0) return fail(MM_ERR_ARG, "num_graphs = 0");
+  if (!d_vbase || !d_ebase) return fail(MM_ERR_ARG, "null vbase / ebase");
+  if (!d_mate && g->n) return fail(MM_ERR_ARG, "null mate");
+  Resolved r;
+  if ((st = resolve(g, o, &r)) != MM_OK) return st;
+  if (r.timing && r.use_graph) return fail(MM_ERR_UNSUPPORTED, "timing with use_graph");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const uint64_t units = (g->n + g->nnz + r.grain - 1) / r.grain;
+  if ((st = ensure_part(g, units)) != MM_OK) return st;
+  SweepParams P = make_params(g, r, d_mate);
+  P.vbase = d_vbase;
+  P.num_graphs = num_graphs;
+  (void)d_ebase;  // entry ranges follow from offsets[vbase[k]]; kept in the ABI for callers
+
+  if (r.use_graph) {
+    BatchGraph& b = g->bg;
+    const bool with_pairs = d_graph_pairs != nullptr;
+    const bool same = b.valid && b.status_bits == (r.word ? 32u : 8u) && b.serial == (uint32_t)r.serial &&
+                      b.grain == r.grain && b.block == (uint32_t)r.block &&
+                      b.blocks_per_sm == (uint32_t)r.blocks_per_sm && b.with_pairs == with_pairs &&
+                      b.num_graphs == num_graphs && units <= g->part_units_cap;
+    if (!same) {
+      if ((st = build_batch_graph(g, r, num_graphs, with_pairs, P, d_graph_pairs)) != MM_OK) return st;
+    } else {
+      if ((st = update_batch_graph(g, r, num_graphs, P, d_graph_pairs)) != MM_OK) return st;
+    }
+    CUDA_TRY(cudaGraphLaunch(b.exec, s));
+    if (r.nosync) return MM_OK;
+    return read_err(g, s);
+  }
+
+  cudaEvent_t* ev = nullptr;
+  if (r.timing) {
+    if ((st = ensure_hist(g)) != MM_OK) return st;
+    ev = next_hist(g, units, d_graph_pairs != nullptr);
+    CUDA_TRY(cudaEventRecord(ev[0], s));
+  }
+  CUDA_TRY(launch_prepare(P, r.word, prepare_grid(g), s, d_graph_pairs, d_graph_pairs ? num_graphs : 0));
+  if (ev) CUDA_TRY(cudaEventRecord(ev[1], s));
+  if (r.serial)
+    CUDA_TRY(launch_serial_batched(P, r.word, s));
+  else
+    CUDA_TRY(launch_sweep(P, r.word, sweep_grid(g, r), r.block, s));
+  if (ev) CUDA_TRY(cudaEventRecord(ev[2], s));
+  if (d_graph_pairs)
+    CUDA_TRY(launch_graph_pairs(d_mate, d_vbase, num_graphs, g->n, d_graph_pairs, prepare_grid(g), s));
+  if (ev) CUDA_TRY(cudaEventRecord(ev[3], s));
+  CUDA_TRY(cudaMemcpyAsync(g->h_err, err_ptr(g), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  if (r.nosync) return MM_OK;
+  return read_err(g, s);
+}
+
+mm_status mm_validate(mm_graph* g, const uint32_t* d_mate, const uint32_t* d_pairs, uint64_t count,
+                      mm_verdict* h_out, void* cuda_stream) {
+  g_err[0] = 0;
+  mm_status st = check_handle(g);
+  if (st != MM_OK) return st;
+  if (!h_out) return fail(MM_ERR_ARG, "null verdict");
+  if (!d_mate && g->n) return fail(MM_ERR_ARG, "null mate");
+  if (d_pairs && count && !g->seen_bits)
+    CUDA_TRY(cudaMalloc(&g->seen_bits, ((g->n + 31) / 32 + 1) * sizeof(uint32_t)));
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  CheckScratch cs{counters_ptr(g), g->seen_bits, g->tile_counts, g->tile_cap};
+  CUDA_TRY(launch_validate(g->n, g->offsets, g->nbrs, d_mate, d_pairs, d_pairs ? count : 0, cs,
+                           prepare_grid(g), s));
+  CUDA_TRY(cudaMemcpyAsync(g->h_counters, counters_ptr(g), 9 * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  const unsigned long long* c = g->h_counters;
+  mm_verdict v{};
+  v.n_matched = c[0];
+  v.n_pairs = c[1];
+  v.n_bad_range = c[2];
+  v.n_asym = c[3];
+  v.n_nonedge = c[4];
+  v.n_uncovered = c[5];
+  v.n_pairs_bad = c[6];
+  v.first_bad_vertex = c[7];
+  v.first_uncovered = c[8];
+  if (v.n_bad_range) v.flags |= MM_V_RANGE;
+  if (v.n_asym) v.flags |= MM_V_ASYM;
+  if (v.n_nonedge) v.flags |= MM_V_NONEDGE;
+  if (v.n_uncovered) v.flags |= MM_V_UNCOVERED;
+  if (d_pairs && (v.n_pairs_bad || count != v.n_pairs)) v.flags |= MM_V_PAIRS;
+  *h_out = v;
+  return MM_OK;
+}
+
+mm_status mm_autotune_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d_vbase,
+                              const int64_t* d_ebase, uint32_t* d_mate_scratch, mm_options* o,
+                              void* cuda_stream) {
+  g_err[0] = 0;
+  mm_status st = check_handle(g);
+  if (st != MM_OK) return st;
+  if (!o || !d_mate_scratch) return fail(MM_ERR_ARG, "null options or scratch");
+  static const uint32_t grains[] = {1024, 2048, 4096, 8192};
+  static const uint32_t bits[] = {8, 32};
+  static const uint32_t blocks[] = {256, 512};
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  float best = 1e30f;
+  mm_options best_o = *o;
+  for (uint32_t gr : grains)
+    for (uint32_t sb : bits)
+      for (uint32_t bt : blocks) {
+        mm_options c = *o;
+        c.grain = gr;
+        c.status_bits = sb;
+        c.block_threads = bt;
+        c.serial = 0;
+        c.use_graph = 0;
+        c.nosync = 0;
+        c.timing = 1;
+        float total = 0;
+        for (int rep = 0; rep < 4; ++rep) {
+          if ((st = mm_skipper_batched(g, num_graphs, d_vbase, d_ebase, &c, d_mate_scratch, nullptr, s)) != MM_OK)
+            return st;
+          mm_timing t;
+          if ((st = mm_get_timing(g, &t)) != MM_OK) return st;
+          if (rep > 0) total += t.total_ms;
+        }
+        mm_verdict v;
+        if ((st = mm_validate(g, d_mate_scratch, nullptr, 0, &v, s)) != MM_OK) return st;
+        if (v.flags) return fail(MM_ERR_CUDA, "autotune candidate gave an invalid matching (flags 0x%x)", v.flags);
+        if (total < best) {
+          best = total;
+          best_o = *o;
+          best_o.grain = gr;
+          best_o.status_bits = sb;
+          best_o.block_threads = bt;
+        }
+      }
+  *o = best_o;
+  return MM_OK;
+}
+
+mm_status mm_destroy(mm_graph* g) {
+  if (!g) return MM_OK;
+  if (g->bg.exec) cudaGraphExecDestroy(g->bg.exec);
+  if (g->bg.graph) cudaGraphDestroy(g->bg.graph);
+  for (auto& e : g->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& set : g->hist)
+    for (auto& e : set)
+      if (e) cudaEventDestroy(e);
+  if (g->state) cudaFree(g->state);
+  if (g->part) cudaFree(g->part);
+  if (g->ctrl) cudaFree(g->ctrl);
+  if (g->seen_bits) cudaFree(g->seen_bits);
+  if (g->tile_counts) cudaFree(g->tile_counts);
+  if (g->h_err) cudaFreeHost(g->h_err);
+  if (g->h_counters) cudaFreeHost(g->h_counters);
+  delete g;
+  return MM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,266 @@
+// check.cu -- CSR input check, the exact maximal-matching checker and the
+// ordered pair-list compaction, on the device.
+//
+// The checker follows the validation rule of Section II-B (every edge touches
+// an output edge; no two output edges share an endpoint) with the counting
+// rules stated in skipper.h, so its verdict can be compared field by field
+// with a host checker.  Counters are aggregated per warp and added with 64-bit
+// atomics; "first offender" fields take the minimum with atomicMin, so every
+// field is independent of thread timing.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace skp {
+
+namespace {
+
+enum { C_MATCHED = 0, C_PAIRS, C_RANGE, C_ASYM, C_NONEDGE, C_UNCOVERED, C_PAIRS_BAD,
+       C_FIRST_BAD, C_FIRST_UNCOVERED, C_COUNT };
+
+__global__ void zero_u64_kernel(unsigned long long* p, uint64_t words, unsigned long long v) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+__global__ void zero_u32_kernel(uint32_t* p, uint64_t words) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    p[i] = 0u;
+}
+
+__global__ void csr_check_kernel(uint64_t n, uint64_t nnz, const int64_t* __restrict__ offsets,
+                                 const uint32_t* __restrict__ nbrs, unsigned long long* bad) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long local = 0;
+  if (tid == 0 && (offsets[0] != 0 || offsets[n] != (int64_t)nnz)) ++local;
+  for (uint64_t i = tid; i < n; i += stride)
+    if (offsets[i] > offsets[i + 1]) ++local;
+  for (uint64_t i = tid; i < nnz; i += stride)
+    if (nbrs[i] >= n) ++local;
+  if (local) atomicAdd(bad, local);
+}
+
+__device__ __forceinline__ void warp_add(unsigned long long* c, uint32_t v) {
+  const uint32_t s = __reduce_add_sync(kFull, v);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(c, (unsigned long long)s);
+}
+
+// vertex pass: range / symmetry / existence of each named partner, and the
+// coverage of every entry of each unmatched row
+__global__ void validate_vertex_kernel(uint64_t n, const int64_t* __restrict__ offsets,
+                                       const uint32_t* __restrict__ nbrs,
+                                       const uint32_t* __restrict__ mate,
+                                       unsigned long long* __restrict__ c) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v0 = (uint64_t)blockIdx.x * blockDim.x; v0 < n; v0 += stride) {
+    const uint64_t v = v0 + threadIdx.x;
+    uint32_t matched = 0, pair = 0, range = 0, asym = 0, nonedge = 0, uncovered = 0;
+    bool bad = false;
+    unsigned long long first_unc = ~0ull;
+    if (v < n) {
+      const uint32_t m = mate[v];
+      if (m != kNone) {
+        if (m >= n || m == v) {
+          range = 1;
+          bad = true;
+        } else {
+          matched = 1;
+          if (mate[m] != (uint32_t)v) {
+            asym = 1;
+            bad = true;
+          } else if (v < m) {
+            pair = 1;
+          }
+          // the edge may be stored in the row of either endpoint
+          bool found = false;
+          for (int64_t i = offsets[v]; i < offsets[v + 1] && !found; ++i) found = nbrs[i] == m;
+          for (int64_t i = offsets[m]; i < offsets[m + 1] && !found; ++i) found = nbrs[i] == (uint32_t)v;
+          if (!found) {
+            nonedge = 1;
+            bad = true;
+          }
+        }
+      } else {
+        for (int64_t i = offsets[v]; i < offsets[v + 1]; ++i) {
+          const uint32_t y = nbrs[i];
+          if (y != (uint32_t)v && y < n && mate[y] == kNone) {
+            ++uncovered;
+            if ((unsigned long long)i < first_unc) first_unc = (unsigned long long)i;
+          }
+        }
+      }
+    }
+    warp_add(c + C_MATCHED, matched);
+    warp_add(c + C_PAIRS, pair);
+    warp_add(c + C_RANGE, range);
+    warp_add(c + C_ASYM, asym);
+    warp_add(c + C_NONEDGE, nonedge);
+    warp_add(c + C_UNCOVERED, uncovered);
+    const uint32_t first_bad = __reduce_min_sync(kFull, bad ? (uint32_t)v : kNone);
+    if ((threadIdx.x & 31) == 0 && first_bad != kNone) atomicMin(c + C_FIRST_BAD, (unsigned long long)first_bad);
+    if (first_unc != ~0ull) atomicMin(c + C_FIRST_UNCOVERED, first_unc);
+  }
+}
+
+__global__ void validate_pairs_kernel(uint64_t n, const uint32_t* __restrict__ mate,
+                                      const uint32_t* __restrict__ pairs, uint64_t count,
+                                      uint32_t* __restrict__ seen, unsigned long long* __restrict__ c) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t j0 = (uint64_t)blockIdx.x * blockDim.x; j0 < count; j0 += stride) {
+    const uint64_t j = j0 + threadIdx.x;
+    uint32_t bad = 0;
+    if (j < count) {
+      const uint32_t a = pairs[2 * j], b = pairs[2 * j + 1];
+      const bool valid = a < b && b < n && mate[a] == b && mate[b] == a;
+      if (!valid) {
+        bad = 1;
+      } else {
+        const uint32_t bit = 1u << (a & 31u);
+        if (atomicOr(seen + (a >> 5), bit) & bit) bad = 1;  // a repeat of a valid pair
+      }
+    }
+    warp_add(c + C_PAIRS_BAD, bad);
+  }
+}
+
+// ---- ordered compaction of (u, mate[u]), u < mate[u] ----
+constexpr int kCompactThreads = 256;
+constexpr int kPerThread = (int)(kCompactTile / kCompactThreads);  // 16
+
+__device__ __forceinline__ bool takes(const uint32_t* mate, uint64_t n, uint64_t u) {
+  if (u >= n) return false;
+  const uint32_t m = mate[u];
+  return m != kNone && m < n && u < m;
+}
+
+__global__ void compact_count_kernel(uint64_t n, const uint32_t* __restrict__ mate,
+                                     uint64_t* __restrict__ tile_counts) {
+  const uint64_t base = (uint64_t)blockIdx.x * kCompactTile + (uint64_t)threadIdx.x * kPerThread;
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int i = 0; i < kPerThread; ++i) cnt += takes(mate, n, base + i);
+  __shared__ uint32_t warp_sums[kCompactThreads / 32];
+  const uint32_t ws = __reduce_add_sync(kFull, cnt);
+  if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = ws;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t t = 0;
+    for (int w = 0; w < kCompactThreads / 32; ++w) t += warp_sums[w];
+    tile_counts[blockIdx.x] = t;
+  }
+}
+
+// exclusive scan of the tile counts in place (one block); total -> *count
+__global__ void compact_scan_kernel(uint64_t tiles, uint64_t* __restrict__ tile_counts,
+                                    uint64_t* __restrict__ count) {
+  __shared__ uint64_t carry_s;
+  __shared__ uint64_t warp_tot[32];
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (uint64_t b = 0; b < tiles; b += blockDim.x) {
+    const uint64_t i = b + threadIdx.x;
+    const uint64_t v = i < tiles ? tile_counts[i] : 0;
+    uint64_t x = v;  // inclusive warp scan
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint64_t y = __shfl_up_sync(kFull, x, d);
+      if ((int)lane >= d) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      uint64_t t = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t y = __shfl_up_sync(kFull, t, d);
+        if ((int)lane >= d) t += y;
+      }
+      if (lane < nw) warp_tot[lane] = t;  // inclusive over warps
+    }
+    __syncthreads();
+    const uint64_t before = carry_s + (wid ? warp_tot[wid - 1] : 0) + x - v;
+    if (i < tiles) tile_counts[i] = before;
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s += warp_tot[nw - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && count) *count = carry_s;
+}
+
+__global__ void compact_scatter_kernel(uint64_t n, const uint32_t* __restrict__ mate,
+                                       const uint64_t* __restrict__ tile_offsets,
+                                       uint32_t* __restrict__ pairs, uint64_t cap) {
+  const uint64_t base = (uint64_t)blockIdx.x * kCompactTile + (uint64_t)threadIdx.x * kPerThread;
+  uint32_t flags = 0, cnt = 0;
+#pragma unroll
+  for (int i = 0; i < kPerThread; ++i)
+    if (takes(mate, n, base + i)) {
+      flags |= 1u << i;
+      ++cnt;
+    }
+  const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t x = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, x, d);
+    if ((int)lane >= d) x += y;
+  }
+  __shared__ uint32_t warp_tot[kCompactThreads / 32];
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  uint32_t wbefore = 0;
+  for (unsigned w = 0; w < wid; ++w) wbefore += warp_tot[w];
+  uint64_t pos = tile_offsets[blockIdx.x] + wbefore + x - cnt;
+#pragma unroll
+  for (int i = 0; i < kPerThread; ++i)
+    if (flags >> i & 1u) {
+      if (pos < cap) {
+        pairs[2 * pos] = (uint32_t)(base + i);
+        pairs[2 * pos + 1] = mate[base + i];
+      }
+      ++pos;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_csr_check(uint64_t n, uint64_t nnz, const int64_t* offsets,
+                             const uint32_t* nbrs, unsigned long long* bad, int grid,
+                             cudaStream_t s) {
+  zero_u64_kernel<<<1, 32, 0, s>>>(bad, 1, 0ull);
+  csr_check_kernel<<<grid, 256, 0, s>>>(n, nnz, offsets, nbrs, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate(uint64_t n, const int64_t* offsets, const uint32_t* nbrs,
+                            const uint32_t* mate, const uint32_t* pairs, uint64_t count,
+                            const CheckScratch& cs, int grid, cudaStream_t s) {
+  zero_u64_kernel<<<1, 32, 0, s>>>(cs.counters, C_FIRST_BAD, 0ull);
+  zero_u64_kernel<<<1, 32, 0, s>>>(cs.counters + C_FIRST_BAD, 2, ~0ull);
+  if (pairs && count) zero_u32_kernel<<<grid, 256, 0, s>>>(cs.seen_bits, (n + 31) / 32);
+  if (n) validate_vertex_kernel<<<grid, 256, 0, s>>>(n, offsets, nbrs, mate, cs.counters);
+  if (pairs && count) validate_pairs_kernel<<<grid, 256, 0, s>>>(n, mate, pairs, count, cs.seen_bits, cs.counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact(uint64_t n, const uint32_t* mate, uint32_t* pairs, uint64_t cap,
+                           uint64_t* count, const CheckScratch& cs, cudaStream_t s) {
+  const uint64_t tiles = (n + kCompactTile - 1) / kCompactTile;
+  if (tiles > cs.block_cap) return cudaErrorInvalidValue;
+  if (tiles == 0) {
+    if (count) zero_u64_kernel<<<1, 32, 0, s>>>(reinterpret_cast<unsigned long long*>(count), 1, 0ull);
+    return cudaGetLastError();
+  }
+  compact_count_kernel<<<(unsigned)tiles, kCompactThreads, 0, s>>>(n, mate, cs.block_counts);
+  compact_scan_kernel<<<1, 1024, 0, s>>>(tiles, cs.block_counts, count);
+  if (pairs && cap)
+    compact_scatter_kernel<<<(unsigned)tiles, kCompactThreads, 0, s>>>(n, mate, cs.block_counts, pairs, cap);
+  return cudaGetLastError();
+}
+
+}  // namespace skp

@@ -1,0 +1,39 @@
+// internal.h -- launchers shared by the translation units of libskipper.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "state.cuh"
+
+namespace skp {
+
+// sweep.cu
+int sweep_blocks_per_sm(bool word, int block_threads);
+cudaError_t launch_prepare(const SweepParams& P, bool word, int grid, cudaStream_t s,
+                           uint64_t* graph_pairs_zero, uint64_t num_graphs);
+cudaError_t launch_sweep(const SweepParams& P, bool word, int grid, int block, cudaStream_t s);
+cudaError_t launch_serial(const SweepParams& P, bool word, cudaStream_t s);
+cudaError_t launch_serial_batched(const SweepParams& P, bool word, cudaStream_t s);
+void get_batched_kernels(bool word, bool serial, const void** prepare, const void** sweep,
+                         const void** pairs);
+cudaError_t launch_graph_pairs(const uint32_t* mate, const int64_t* vbase, uint64_t num_graphs,
+                               uint64_t n, uint64_t* graph_pairs, int grid, cudaStream_t s);
+
+// check.cu
+struct CheckScratch {
+  unsigned long long* counters;  // mm_verdict-shaped device block (see check.cu)
+  uint32_t* seen_bits;           // ceil(n/32) words
+  uint64_t* block_counts;        // compaction: one count per tile of vertices
+  uint64_t block_cap;
+};
+cudaError_t launch_csr_check(uint64_t n, uint64_t nnz, const int64_t* offsets,
+                             const uint32_t* nbrs, unsigned long long* bad, int grid,
+                             cudaStream_t s);
+cudaError_t launch_validate(uint64_t n, const int64_t* offsets, const uint32_t* nbrs,
+                            const uint32_t* mate, const uint32_t* pairs, uint64_t count,
+                            const CheckScratch& cs, int grid, cudaStream_t s);
+constexpr uint64_t kCompactTile = 4096;  // vertices per compaction tile
+cudaError_t launch_compact(uint64_t n, const uint32_t* mate, uint32_t* pairs, uint64_t cap,
+                           uint64_t* count, const CheckScratch& cs, cudaStream_t s);
+
+}  // namespace skp

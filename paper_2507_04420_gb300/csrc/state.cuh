@@ -1,0 +1,214 @@
+// state.cuh -- per-vertex state machine of Skipper (Section IV-B, Fig. 4;
+// Algorithm 1) on GB300 global memory.
+//
+// Two layouts of the state array:
+//   ByteState: one byte per vertex (ACC = 0, RSVD = 1, MCHD = 2 as in
+//     Algorithm 1), four vertices packed in a 32-bit word.  Every access is a
+//     32-bit access to the whole word (relaxed loads, 32-bit CAS, 32-bit
+//     XOR), so all accesses to a location have the same size and are
+//     morally strong in the PTX memory model.  A byte CAS is a word CAS that
+//     is retried when only a neighbouring byte changed.  The holder-only
+//     transitions RSVD->MCHD and RSVD->ACC (Algorithm 1 lines 15 and 18, plain
+//     stores in the paper) become one atomic XOR on the word, which cannot
+//     disturb the neighbouring bytes.
+//   WordState: one 32-bit word per vertex that doubles as the mate entry:
+//     ACC = 0xFFFFFFFF (= unmatched), RSVD = 0xFFFFFFFE, MCHD = the partner id.
+//     Claiming v writes u into v's word directly; the holder then stores v into
+//     u's word.  No separate mate array is needed.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace skp {
+
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kAcc = 0u, kRsvd = 1u, kMchd = 2u;         // byte states
+constexpr uint32_t kWAcc = 0xFFFFFFFFu, kWRsvd = 0xFFFFFFFEu;  // word states
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// device error word bits
+constexpr uint32_t kErrTimeout = 1u;
+constexpr uint32_t kErrBadId = 2u;
+
+struct SweepParams {
+  uint64_t n;
+  uint64_t nnz;
+  const int64_t* offsets;
+  const uint32_t* nbrs;
+  uint32_t* state;      // ByteState: ceil(n/4) packed words; WordState: == mate
+  uint32_t* mate;
+  int64_t* part;        // merge-path unit starts: (row, entry) for units+1 diagonals
+  uint64_t units;
+  uint64_t grain;
+  unsigned long long* work;  // next unit to hand out
+  uint32_t* err;
+  uint64_t spin_limit;
+  uint64_t poison;      // vertex + 1 left RESERVED after init (fault injection), 0 = off
+  // batched serial mode
+  const int64_t* vbase;
+  uint64_t num_graphs;
+};
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Relaxed load without a compiler memory fence: used by the filter that only
+// decides whether an entry is worth an attempt (a stale value there costs an
+// extra attempt, never a wrong result, since MCHD is absorbing).
+__device__ __forceinline__ uint32_t ld_relaxed_nf(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Streaming 128-bit load of four neighbour ids: read-only for the kernel's
+// lifetime, not kept in L1, first to leave L2.
+__device__ __forceinline__ uint4 ld_stream_v4(const uint32_t* p, uint64_t policy) {
+  uint4 r;
+  asm volatile(
+      "ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+      : "l"(p), "l"(policy));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p, uint64_t policy) {
+  uint32_t r;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;"
+               : "=r"(r)
+               : "l"(p), "l"(policy));
+  return r;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// Bounded wait with exponential back-off.  Returns false when the wait has
+// run past its limit or another thread has already reported an error.
+struct Waiter {
+  uint64_t polls = 0;
+  uint32_t ns = 32;
+  __device__ __forceinline__ bool wait(const SweepParams& P) {
+    ++polls;
+    if (polls > P.spin_limit) {
+      atomicOr(P.err, kErrTimeout);
+      return false;
+    }
+    if ((polls & 63) == 0 && ld_relaxed(P.err) != 0) return false;
+    __nanosleep(ns);
+    ns = ns < 1024 ? ns * 2 : 1024;
+    return true;
+  }
+};
+
+struct ByteState {
+  uint32_t* words;
+  uint32_t* mate;
+  __device__ explicit ByteState(const SweepParams& P) : words(P.state), mate(P.mate) {}
+  __device__ static __forceinline__ uint32_t shift(uint32_t v) { return (v & 3u) << 3; }
+  // state byte of v
+  __device__ __forceinline__ uint32_t load(uint32_t v) const {
+    return (ld_relaxed(words + (v >> 2)) >> shift(v)) & 0xFFu;
+  }
+  __device__ __forceinline__ uint32_t peek(uint32_t v) const {
+    return (ld_relaxed_nf(words + (v >> 2)) >> shift(v)) & 0xFFu;
+  }
+  __device__ static __forceinline__ bool matched(uint32_t s) { return s == kMchd; }
+  // Byte CAS from `expect` to `desired`; a failure caused by a neighbouring
+  // byte is retried (it is not a conflict on v).
+  __device__ __forceinline__ bool cas(uint32_t v, uint32_t expect, uint32_t desired,
+                                      const SweepParams& P) const {
+    uint32_t* w = words + (v >> 2);
+    const uint32_t sh = shift(v);
+    uint32_t cur = ld_relaxed(w);
+    for (uint64_t tries = 0;; ++tries) {
+      if (((cur >> sh) & 0xFFu) != expect) return false;
+      const uint32_t next = (cur & ~(0xFFu << sh)) | (desired << sh);
+      const uint32_t old = atomicCAS(w, cur, next);
+      if (old == cur) return true;
+      cur = old;
+      if (tries > P.spin_limit) {  // lock-free retry; bounded all the same
+        atomicOr(P.err, kErrTimeout);
+        return false;
+      }
+    }
+  }
+  __device__ __forceinline__ bool reserve(uint32_t u, const SweepParams& P) const {
+    return cas(u, kAcc, kRsvd, P);
+  }
+  __device__ __forceinline__ bool claim(uint32_t v, uint32_t /*u*/, const SweepParams& P) const {
+    return cas(v, kAcc, kMchd, P);
+  }
+  // holder only: RSVD -> MCHD, record the pair
+  __device__ __forceinline__ void commit(uint32_t u, uint32_t v) const {
+    mate[u] = v;
+    mate[v] = u;
+    atomicXor(words + (u >> 2), (kRsvd ^ kMchd) << shift(u));
+  }
+  // holder only: RSVD -> ACC
+  __device__ __forceinline__ void release(uint32_t u) const {
+    atomicXor(words + (u >> 2), (kRsvd ^ kAcc) << shift(u));
+  }
+};
+
+struct WordState {
+  uint32_t* words;
+  __device__ explicit WordState(const SweepParams& P) : words(P.state) {}
+  __device__ __forceinline__ uint32_t load(uint32_t v) const { return ld_relaxed(words + v); }
+  __device__ __forceinline__ uint32_t peek(uint32_t v) const { return ld_relaxed_nf(words + v); }
+  __device__ static __forceinline__ bool matched(uint32_t s) { return s < kWRsvd; }
+  __device__ __forceinline__ bool reserve(uint32_t u, const SweepParams&) const {
+    return atomicCAS(words + u, kWAcc, kWRsvd) == kWAcc;
+  }
+  __device__ __forceinline__ bool claim(uint32_t v, uint32_t u, const SweepParams&) const {
+    return atomicCAS(words + v, kWAcc, u) == kWAcc;
+  }
+  __device__ __forceinline__ void commit(uint32_t u, uint32_t v) const { st_relaxed(words + u, v); }
+  __device__ __forceinline__ void release(uint32_t u) const { st_relaxed(words + u, kWAcc); }
+};
+
+// Algorithm 1, lines 6-18, for one stored entry (x, y).  Returns true when the
+// row vertex x is MCHD at the end (by this attempt or by another thread), which
+// lets the caller leave the rest of row x.
+template <class S>
+__device__ __forceinline__ bool resolve_edge(const S& s, uint32_t x, uint32_t y,
+                                             const SweepParams& P) {
+  if (x == y) return S::matched(s.load(x));  // lines 6-7: loops are skipped
+  const uint32_t u = x < y ? x : y;          // lines 8-9: lower id reserved first
+  const uint32_t v = x < y ? y : x;
+  Waiter wt;
+  for (;;) {
+    const uint32_t su = s.load(u);           // line 10
+    const uint32_t sv = s.load(v);
+    if (S::matched(su) || S::matched(sv)) return S::matched(x == u ? su : sv);
+    if (!s.reserve(u, P)) {                  // lines 11-12: retry the outer test
+      if (!wt.wait(P)) return false;
+      continue;
+    }
+    for (;;) {                               // lines 13-16, holding u
+      if (S::matched(s.load(v))) break;
+      if (s.claim(v, u, P)) {
+        s.commit(u, v);                      // lines 15-16
+        return true;
+      }
+      if (!wt.wait(P)) {
+        s.release(u);
+        return false;
+      }
+    }
+    s.release(u);                            // lines 17-18: v went to another edge
+    return x == v;
+  }
+}
+
+}  // namespace skp

@@ -1,0 +1,298 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle.
+
+Skipper's parallel result is any maximal matching (Section V-C: the output
+varies between runs), so parallel runs are compared by the exact checker:
+the oracle's verdict and the device checker's verdict must be identical field
+by field, and both must say "valid maximal matching".  Where every maximal
+matching is the same size (K_{a,b}, stars, K_n) or unique (disjoint edges),
+the size or the bytes are compared too.  Serial mode walks rows and
+neighbours in SGMM order and must reproduce SGMM byte for byte.
+"""
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+import oracle
+from tests.conftest import cuda_ok
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not cuda_ok(), reason="needs a CUDA GPU")]
+
+NONE = 0xFFFFFFFF
+
+
+@pytest.fixture(scope="module")
+def skp():
+    import paper_2507_04420_gb300 as m
+    torch.cuda.set_device(0)
+    return m
+
+
+def _np(t):
+    return t.cpu().numpy().view(np.uint32) if t.dtype == torch.int32 else t.cpu().numpy()
+
+
+def run(skp, csr, **kw):
+    """Run through the C ABI; return (mate, pairs, oracle verdict, device verdict)."""
+    off, nb = csr.offsets.numpy(), csr.nbrs.numpy()
+    d = csr.to("cuda")
+    with skp.Graph(d.offsets, d.nbrs) as h:
+        mate, pairs, cnt = h.skipper(pairs=True, **kw)
+        k = int(cnt.item())
+        m = _np(mate)
+        p = _np(pairs[:k]).reshape(-1, 2)
+        vr = oracle.check(off, nb, m, p)
+        vd = h.validate(mate, pairs[:k])
+    return m, p, vr, vd
+
+
+def assert_parity(vr, vd):
+    assert vr.flags == 0, vr.as_dict()
+    assert vd.as_dict() == vr.as_dict()
+
+
+SMALL = {
+    "fig1": lambda: gg.from_edges(4, torch.tensor([0, 0, 0, 1, 2]), torch.tensor([1, 2, 3, 2, 3])),
+    "path101": lambda: gg.path(101),
+    "star64": lambda: gg.star(64),
+    "k3_17": lambda: gg.complete_bipartite(3, 17),
+    "disjoint50": lambda: gg.disjoint_edges(50),
+    "k9": lambda: gg.complete(9),
+    "grid16x32": lambda: gg.grid(16, 32),
+    "rmat10": lambda: gg.rmat(10, 16, seed=2),
+    "er2k": lambda: gg.erdos_renyi(2000, 9000, seed=3),
+}
+
+
+@pytest.mark.parametrize("bits", [8, 32])
+@pytest.mark.parametrize("name", sorted(SMALL))
+def test_serial_equals_sgmm(skp, name, bits):
+    csr = SMALL[name]()
+    ref_mate, ref_pairs = oracle.sgmm(csr.offsets.numpy(), csr.nbrs.numpy())
+    m, p, vr, vd = run(skp, csr, status_bits=bits, serial=1)
+    assert np.array_equal(m, ref_mate)
+    assert np.array_equal(p, ref_pairs)   # ascending u = SGMM's push order on a symmetric CSR
+    assert_parity(vr, vd)
+
+
+@pytest.mark.parametrize("bits", [8, 32])
+@pytest.mark.parametrize("name", sorted(SMALL))
+def test_parallel_valid_and_verdicts_identical(skp, name, bits):
+    csr = SMALL[name]()
+    _, ref_pairs = oracle.sgmm(csr.offsets.numpy(), csr.nbrs.numpy())
+    for grain in (128, 2048):
+        m, p, vr, vd = run(skp, csr, status_bits=bits, grain=grain)
+        assert_parity(vr, vd)
+        assert 2 * len(p) >= len(ref_pairs)
+        if name == "star64":
+            assert len(p) == 1
+        if name == "k3_17":
+            assert len(p) == 3
+        if name == "k9":
+            assert len(p) == 4
+        if name == "disjoint50":
+            assert m.tolist() == [v ^ 1 for v in range(100)]
+
+
+@pytest.mark.parametrize("bits", [8, 32])
+def test_er_100k_1m(skp, bits):
+    """Erdos-Renyi n=100,000, m=1,000,000 (2M directed entries)."""
+    csr = gg.erdos_renyi(100_000, 1_000_000, seed=1)
+    ref_mate, ref_pairs = oracle.sgmm(csr.offsets.numpy(), csr.nbrs.numpy())
+    m, p, vr, vd = run(skp, csr, status_bits=bits, serial=1)
+    assert np.array_equal(m, ref_mate)
+    assert_parity(vr, vd)
+    for grain in (256, 2048, 8192):
+        m, p, vr, vd = run(skp, csr, status_bits=bits, grain=grain)
+        assert_parity(vr, vd)
+        assert 2 * len(p) >= len(ref_pairs)
+
+
+@pytest.mark.parametrize("bits", [8, 32])
+@pytest.mark.parametrize("block", [32, 256, 512])
+def test_launch_shapes(skp, bits, block):
+    csr = gg.rmat(14, 16, seed=9)
+    for bps in (0, 1):
+        m, p, vr, vd = run(skp, csr, status_bits=bits, block_threads=block, blocks_per_sm=bps)
+        assert_parity(vr, vd)
+
+
+def _manual(n, rows):
+    off = [0]
+    nb = []
+    for r in rows:
+        nb.extend(r)
+        off.append(len(nb))
+    assert len(off) == n + 1
+    return gg.CSR(torch.tensor(off, dtype=torch.int64), torch.tensor(nb, dtype=torch.int32))
+
+
+def test_loops_unsorted_rows_and_ragged_tail(skp):
+    # self-loops, rows in arbitrary order, nnz = 13 (not a multiple of 4)
+    csr = _manual(6, [[0, 3, 1], [0, 1, 2], [5, 1], [0, 3, 4], [3], [2]])
+    ref_mate, _ = oracle.sgmm(csr.offsets.numpy(), csr.nbrs.numpy())
+    for bits in (8, 32):
+        m, p, vr, vd = run(skp, csr, status_bits=bits, serial=1)
+        assert np.array_equal(m, ref_mate)
+        assert_parity(vr, vd)
+        for grain in (128, 256):
+            m, p, vr, vd = run(skp, csr, status_bits=bits, grain=grain)
+            assert_parity(vr, vd)
+
+
+def test_edges_stored_once(skp):
+    """Non-symmetric CSR: each edge only in the row of its lower end (Section V-C)."""
+    g = gg.rmat(12, 8, seed=4)
+    off, nb = g.offsets.numpy(), g.nbrs.numpy()
+    rows = np.repeat(np.arange(g.n), np.diff(off))
+    keep = nb > rows
+    cnt = np.bincount(rows[keep], minlength=g.n)
+    off2 = np.zeros(g.n + 1, dtype=np.int64)
+    off2[1:] = np.cumsum(cnt)
+    csr = gg.CSR(torch.from_numpy(off2), torch.from_numpy(nb[keep].copy()))
+    for bits in (8, 32):
+        m, p, vr, vd = run(skp, csr, status_bits=bits)
+        assert_parity(vr, vd)
+        ref_mate, _ = oracle.sgmm(off2, nb[keep])
+        m, p, vr, vd = run(skp, csr, status_bits=bits, serial=1)
+        assert np.array_equal(m, ref_mate)
+
+
+def test_empty_rows_and_tiny_graphs(skp):
+    # long runs of isolated vertices between short rows
+    n = 3000
+    u = torch.tensor([0, 1, 500, 501, 502, 2990, 2999, 1500], dtype=torch.int64)
+    v = torch.tensor([1, 2, 501, 502, 503, 2999, 1500, 1000], dtype=torch.int64)
+    csr = gg.from_edges(n, u, v)
+    ref_mate, _ = oracle.sgmm(csr.offsets.numpy(), csr.nbrs.numpy())
+    for bits in (8, 32):
+        m, p, vr, vd = run(skp, csr, status_bits=bits, serial=1)
+        assert np.array_equal(m, ref_mate)
+        for grain in (128, 2048):
+            m, p, vr, vd = run(skp, csr, status_bits=bits, grain=grain)
+            assert_parity(vr, vd)
+    # no edges at all, and a single vertex
+    for n in (1, 7):
+        csr = gg.CSR(torch.zeros(n + 1, dtype=torch.int64), torch.zeros(0, dtype=torch.int32))
+        m, p, vr, vd = run(skp, csr)
+        assert m.tolist() == [NONE] * n and len(p) == 0
+        assert_parity(vr, vd)
+
+
+def test_misaligned_and_bad_graphs(skp):
+    csr = gg.path(9).to("cuda")
+    buf = torch.zeros(csr.nnz + 1, dtype=torch.int32, device="cuda")
+    buf[1:] = csr.nbrs
+    with pytest.raises(skp.SkipperError) as e:
+        skp.Graph(csr.offsets, buf[1:])
+    assert e.value.status == "MM_ERR_ARG"
+    bad = csr.nbrs.clone()
+    bad[3] = 9                       # id >= n
+    with pytest.raises(skp.SkipperError) as e:
+        skp.Graph(csr.offsets, bad)
+    assert e.value.status == "MM_ERR_BAD_GRAPH"
+    off = csr.offsets.clone()
+    off[4], off[5] = off[5], off[4]  # not monotone
+    with pytest.raises(skp.SkipperError) as e:
+        skp.Graph(off, csr.nbrs)
+    assert e.value.status == "MM_ERR_BAD_GRAPH"
+    with pytest.raises(skp.SkipperError) as e:
+        skp.Graph(csr.offsets, csr.nbrs).skipper(status_bits=16)
+    assert e.value.status == "MM_ERR_ARG"
+
+
+@pytest.mark.parametrize("bits", [8, 32])
+def test_wait_limit_reports_timeout_and_context_survives(skp, bits):
+    """A vertex left RESERVED by no thread: every wait on it runs out, the call
+    returns MM_ERR_TIMEOUT (no trap, no hang), and the next call is normal."""
+    csr = gg.rmat(12, 8, seed=6)
+    d = csr.to("cuda")
+    hub = int(torch.argmax(csr.offsets[1:] - csr.offsets[:-1]))
+    with skp.Graph(d.offsets, d.nbrs) as h:
+        for serial in (0, 1):
+            with pytest.raises(skp.SkipperError) as e:
+                h.skipper(status_bits=bits, serial=serial, poison_vertex=hub + 1, spin_limit=2000)
+            assert e.value.status == "MM_ERR_TIMEOUT"
+        mate = h.skipper(status_bits=bits)
+        v = h.validate(mate)
+        assert v.flags == 0
+
+
+def test_validator_parity_on_corrupted_results(skp):
+    csr = gg.erdos_renyi(3000, 12000, seed=8)
+    off, nb = csr.offsets.numpy(), csr.nbrs.numpy()
+    good, pairs = oracle.sgmm(off, nb)
+    d = csr.to("cuda")
+    rng = np.random.default_rng(0)
+    cases = []
+    m = good.copy(); a, b = pairs[5]; m[a] = m[b] = NONE; cases.append((m, None))      # uncovered
+    m = good.copy(); m[pairs[7][0]] = NONE; cases.append((m, None))                    # asymmetric
+    m = good.copy(); m[pairs[9][0]] = 2999 if pairs[9][0] != 2999 else 0; cases.append((m, None))
+    m = good.copy(); m[11] = 1 << 30; cases.append((m, None))                          # out of range
+    m = good.copy(); m[12] = 12; cases.append((m, None))                               # self
+    m = good.copy(); unmatched = np.flatnonzero(m == NONE)
+    if len(unmatched) >= 2:
+        m[unmatched[0]], m[unmatched[1]] = unmatched[1], unmatched[0]                  # non-edge pair
+    cases.append((m, None))
+    cases.append((good, pairs[:-1]))                                                   # missing pair
+    cases.append((good, np.vstack([pairs, pairs[:2]])))                                # repeats
+    cases.append((good, pairs[:, ::-1].copy()))                                        # (high, low)
+    cases.append((good, rng.permutation(pairs)))                                       # any order
+    with skp.Graph(d.offsets, d.nbrs) as h:
+        for m, p in cases:
+            vr = oracle.check(off, nb, m, p)
+            dm = torch.from_numpy(m.view(np.int32)).cuda()
+            dp = None if p is None else torch.from_numpy(np.ascontiguousarray(p).astype(np.uint32).view(np.int32)).cuda()
+            vd = h.validate(dm, dp)
+            assert vd.as_dict() == vr.as_dict()
+        assert sum(oracle.check(off, nb, m, p).flags != 0 for m, p in cases) == len(cases) - 1
+
+
+def test_pairs_cap_nosync_and_timing(skp):
+    csr = gg.rmat(13, 16, seed=12).to("cuda")
+    with skp.Graph(csr.offsets, csr.nbrs) as h:
+        mate, pairs, cnt = h.skipper(pairs=True, timing=1)
+        t = h.timing()
+        assert t["sweep_ms"] > 0 and t["units"] > 0
+        k = int(cnt.item())
+        mate2, pairs2, cnt2 = h.skipper(pairs=True, cap=5, serial=1)
+        assert int(cnt2.item()) >= 5
+        mate3, pairs3, cnt3 = h.skipper(pairs=True, serial=1)
+        assert torch.equal(pairs2[:5], pairs3[:5])
+        m = h.skipper(nosync=1)
+        h.sync()
+        assert h.validate(m).flags == 0
+        # pairs list == {(u, mate[u]) : u < mate[u]} in ascending u
+        mm = _np(mate).astype(np.int64)
+        us = np.flatnonzero((mm != NONE) & (np.arange(len(mm)) < mm))
+        assert np.array_equal(_np(pairs[:k]).reshape(-1, 2)[:, 0], us)
+
+
+@pytest.mark.parametrize("bits", [8, 32])
+def test_contention_shapes_and_rmat22(skp, bits):
+    """RMAT scale 22 (ef 16), star with 1M leaves, path of 4M vertices,
+    K_{2048,2048} and a 2048x2048 grid: verdicts identical to the oracle's."""
+    shapes = {
+        "rmat22": lambda: gg.rmat(22, 16, seed=1, device="cuda"),
+        "star1m": lambda: gg.star(1_000_000, device="cuda"),
+        "path4m": lambda: gg.path(4_000_000, device="cuda"),
+        "k2048": lambda: gg.complete_bipartite(2048, 2048, device="cuda"),
+        "grid2048": lambda: gg.grid(2048, 2048, device="cuda"),
+    }
+    for name, make in shapes.items():
+        d = make()
+        off, nb = d.offsets.cpu().numpy(), d.nbrs.cpu().numpy()
+        _, ref_pairs = oracle.sgmm(off, nb)
+        with skp.Graph(d.offsets, d.nbrs) as h:
+            mate, pairs, cnt = h.skipper(status_bits=bits, pairs=True)
+            k = int(cnt.item())
+            vr = oracle.check(off, nb, _np(mate), _np(pairs[:k]).reshape(-1, 2))
+            vd = h.validate(mate, pairs[:k])
+        assert_parity(vr, vd)
+        assert 2 * k >= len(ref_pairs), name
+        if name == "star1m":
+            assert k == 1
+        if name == "k2048":
+            assert k == 2048
+        del d
+        torch.cuda.empty_cache()
