@@ -111,31 +111,37 @@ struct Waiter {
   }
 };
 
+// State layouts.  `raw(v)` is the 32-bit word that holds v's state (the
+// whole packed word for ByteState); `matched(raw, v)` reads v's state out of
+// such a word.  try_reserve / try_claim start from a word the caller has
+// already observed and, when they fail, leave in it the word the CAS met, so
+// a failed attempt costs no extra load.
 struct ByteState {
   uint32_t* words;
   uint32_t* mate;
   __device__ explicit ByteState(const SweepParams& P) : words(P.state), mate(P.mate) {}
   __device__ static __forceinline__ uint32_t shift(uint32_t v) { return (v & 3u) << 3; }
-  // state byte of v
-  __device__ __forceinline__ uint32_t load(uint32_t v) const {
-    return (ld_relaxed(words + (v >> 2)) >> shift(v)) & 0xFFu;
+  __device__ __forceinline__ uint32_t raw(uint32_t v) const { return ld_relaxed(words + (v >> 2)); }
+  __device__ __forceinline__ uint32_t peek(uint32_t v) const { return ld_relaxed_nf(words + (v >> 2)); }
+  __device__ static __forceinline__ bool matched(uint32_t raw, uint32_t v) {
+    return ((raw >> shift(v)) & 0xFFu) == kMchd;
   }
-  __device__ __forceinline__ uint32_t peek(uint32_t v) const {
-    return (ld_relaxed_nf(words + (v >> 2)) >> shift(v)) & 0xFFu;
-  }
-  __device__ static __forceinline__ bool matched(uint32_t s) { return s == kMchd; }
-  // Byte CAS from `expect` to `desired`; a failure caused by a neighbouring
-  // byte is retried (it is not a conflict on v).
-  __device__ __forceinline__ bool cas(uint32_t v, uint32_t expect, uint32_t desired,
+  // Byte CAS from `expect` to `desired` starting at the observed word `cur`; a
+  // failure caused only by a neighbouring byte is retried (it is not a
+  // conflict on v).  On failure `cur` holds the word whose byte for v is not
+  // `expect`.
+  __device__ __forceinline__ bool cas(uint32_t v, uint32_t expect, uint32_t desired, uint32_t& cur,
                                       const SweepParams& P) const {
     uint32_t* w = words + (v >> 2);
     const uint32_t sh = shift(v);
-    uint32_t cur = ld_relaxed(w);
     for (uint64_t tries = 0;; ++tries) {
       if (((cur >> sh) & 0xFFu) != expect) return false;
       const uint32_t next = (cur & ~(0xFFu << sh)) | (desired << sh);
       const uint32_t old = atomicCAS(w, cur, next);
-      if (old == cur) return true;
+      if (old == cur) {
+        cur = next;
+        return true;
+      }
       cur = old;
       if (tries > P.spin_limit) {  // lock-free retry; bounded all the same
         atomicOr(P.err, kErrTimeout);
@@ -143,11 +149,12 @@ struct ByteState {
       }
     }
   }
-  __device__ __forceinline__ bool reserve(uint32_t u, const SweepParams& P) const {
-    return cas(u, kAcc, kRsvd, P);
+  __device__ __forceinline__ bool try_reserve(uint32_t u, uint32_t& ru, const SweepParams& P) const {
+    return cas(u, kAcc, kRsvd, ru, P);
   }
-  __device__ __forceinline__ bool claim(uint32_t v, uint32_t /*u*/, const SweepParams& P) const {
-    return cas(v, kAcc, kMchd, P);
+  __device__ __forceinline__ bool try_claim(uint32_t v, uint32_t /*u*/, uint32_t& rv,
+                                            const SweepParams& P) const {
+    return cas(v, kAcc, kMchd, rv, P);
   }
   // holder only: RSVD -> MCHD, record the pair
   __device__ __forceinline__ void commit(uint32_t u, uint32_t v) const {
@@ -164,50 +171,58 @@ struct ByteState {
 struct WordState {
   uint32_t* words;
   __device__ explicit WordState(const SweepParams& P) : words(P.state) {}
-  __device__ __forceinline__ uint32_t load(uint32_t v) const { return ld_relaxed(words + v); }
+  __device__ __forceinline__ uint32_t raw(uint32_t v) const { return ld_relaxed(words + v); }
   __device__ __forceinline__ uint32_t peek(uint32_t v) const { return ld_relaxed_nf(words + v); }
-  __device__ static __forceinline__ bool matched(uint32_t s) { return s < kWRsvd; }
-  __device__ __forceinline__ bool reserve(uint32_t u, const SweepParams&) const {
-    return atomicCAS(words + u, kWAcc, kWRsvd) == kWAcc;
+  __device__ static __forceinline__ bool matched(uint32_t raw, uint32_t) { return raw < kWRsvd; }
+  __device__ __forceinline__ bool try_reserve(uint32_t u, uint32_t& ru, const SweepParams&) const {
+    ru = atomicCAS(words + u, kWAcc, kWRsvd);
+    return ru == kWAcc;
   }
-  __device__ __forceinline__ bool claim(uint32_t v, uint32_t u, const SweepParams&) const {
-    return atomicCAS(words + v, kWAcc, u) == kWAcc;
+  __device__ __forceinline__ bool try_claim(uint32_t v, uint32_t u, uint32_t& rv,
+                                            const SweepParams&) const {
+    rv = atomicCAS(words + v, kWAcc, u);
+    return rv == kWAcc;
   }
   __device__ __forceinline__ void commit(uint32_t u, uint32_t v) const { st_relaxed(words + u, v); }
   __device__ __forceinline__ void release(uint32_t u) const { st_relaxed(words + u, kWAcc); }
 };
 
-// Algorithm 1, lines 6-18, for one stored entry (x, y).  Returns true when the
-// row vertex x is MCHD at the end (by this attempt or by another thread), which
-// lets the caller leave the rest of row x.
+// Algorithm 1, lines 6-18, for one stored entry (x, y), given words rx, ry
+// already observed for x and y (they stand for the first line-10 read).
+// Returns true when the row vertex x is MCHD at the end (by this attempt or by
+// another thread), which lets the caller leave the rest of row x.
 template <class S>
-__device__ __forceinline__ bool resolve_edge(const S& s, uint32_t x, uint32_t y,
-                                             const SweepParams& P) {
-  if (x == y) return S::matched(s.load(x));  // lines 6-7: loops are skipped
-  const uint32_t u = x < y ? x : y;          // lines 8-9: lower id reserved first
-  const uint32_t v = x < y ? y : x;
+__device__ __forceinline__ bool resolve_edge(const S& s, uint32_t x, uint32_t y, uint32_t rx,
+                                             uint32_t ry, const SweepParams& P) {
+  if (x == y) return S::matched(rx, x);      // lines 6-7: loops are skipped
+  const bool x_low = x < y;                  // lines 8-9: lower id reserved first
+  const uint32_t u = x_low ? x : y, v = x_low ? y : x;
+  uint32_t ru = x_low ? rx : ry, rv = x_low ? ry : rx;
   Waiter wt;
   for (;;) {
-    const uint32_t su = s.load(u);           // line 10
-    const uint32_t sv = s.load(v);
-    if (S::matched(su) || S::matched(sv)) return S::matched(x == u ? su : sv);
-    if (!s.reserve(u, P)) {                  // lines 11-12: retry the outer test
+    // line 10
+    if (S::matched(ru, u) || S::matched(rv, v)) return S::matched(x_low ? ru : rv, x);
+    if (!s.try_reserve(u, ru, P)) {          // lines 11-12: wait, then re-test line 10
+      if (S::matched(ru, u)) return x_low;
       if (!wt.wait(P)) return false;
+      ru = s.raw(u);
+      rv = s.raw(v);
       continue;
     }
     for (;;) {                               // lines 13-16, holding u
-      if (S::matched(s.load(v))) break;
-      if (s.claim(v, u, P)) {
+      if (s.try_claim(v, u, rv, P)) {
         s.commit(u, v);                      // lines 15-16
         return true;
       }
+      if (S::matched(rv, v)) break;          // v went to another edge
       if (!wt.wait(P)) {
         s.release(u);
         return false;
       }
+      rv = s.raw(v);
     }
-    s.release(u);                            // lines 17-18: v went to another edge
-    return x == v;
+    s.release(u);                            // lines 17-18
+    return !x_low;
   }
 }
 

@@ -34,23 +34,6 @@ __device__ __forceinline__ uint32_t pick4(const uint32_t (&a)[4], int j) {
   return r;
 }
 
-__device__ __forceinline__ int64_t row_end_or_max(const SweepParams& P, int64_t r) {
-  // offsets[r] for r <= n; rows past the last one never end
-  return r <= (int64_t)P.n ? __ldg(P.offsets + r) : INT64_MAX;
-}
-
-// number of lanes k whose ascending value end_k is <= e; the caller guarantees
-// end_31 > e, so the count is at most 31.
-__device__ __forceinline__ int count_le(int64_t my_end, int64_t e) {
-  int c = 0;
-#pragma unroll
-  for (int step = 16; step >= 1; step >>= 1) {
-    const int64_t v = __shfl_sync(kFull, my_end, c + step - 1);
-    if (v <= e) c += step;
-  }
-  return c;
-}
-
 // Merge-path split of diagonal d over the row ends offsets[1..n] and the entry
 // indices 0..nnz-1 (a row end equal to an entry index is taken first): returns
 // the number of rows finished before the split; entry index = d - rows.
@@ -100,41 +83,83 @@ __global__ void prepare_kernel(SweepParams P, uint64_t* graph_pairs, uint64_t nu
   }
 }
 
+// number of lanes k whose ascending value rel_k is <= p (32-bit); the caller
+// guarantees rel_31 > p for the lanes whose answer it uses.
+__device__ __forceinline__ int count_le(int rel, int p) {
+  int c = 0;
+#pragma unroll
+  for (int step = 16; step >= 1; step >>= 1) {
+    const int v = __shfl_sync(kFull, rel, c + step - 1);
+    if (v <= p) c += step;
+  }
+  return c;
+}
+
 // One work unit: entries [pos, e_end), the first of which lies in row >= row0.
+//
+// The warp keeps a window of 32 consecutive rows: lane k holds the end offset
+// of row wbase+k and the word holding that row vertex's state, both loaded in
+// one coalesced step, and `mchd` has bit k set when row wbase+k is known to be
+// matched.  Matched rows are jumped over with bit arithmetic, so a matched
+// source costs no load of its own (Skipper leaves the rest of a matched row;
+// SGMM does the same in CSR order, Section II-B).  The unmatched entries are
+// read in chunks of up to 128 (one aligned 128-bit load per lane); the state
+// of the row at the head of each chunk is re-read alongside, so a long row
+// matched by another warp is left after at most one more chunk.
 template <class S>
 __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int64_t row0,
                                            int64_t pos, const int64_t e_end, const unsigned lane,
                                            const uint64_t pol_stream) {
-  int64_t wbase = row0;                                // window: rows wbase .. wbase+31
-  int64_t my_end = row_end_or_max(P, wbase + 1 + lane);  // lane k: end of row wbase+k
   const uint32_t n32 = (uint32_t)P.n;
+  int64_t wbase = row0;
+  int64_t my_end;
+  uint32_t my_st;
+  unsigned mchd;
+  {
+    const int64_t r = wbase + lane;
+    const bool in = r < (int64_t)P.n;
+    my_end = in ? __ldg(P.offsets + r + 1) : INT64_MAX;
+    my_st = in ? s.peek((uint32_t)r) : 0u;
+    mchd = __ballot_sync(kFull, !in || S::matched(my_st, (uint32_t)r));  // rows past n hold no entries
+  }
   while (pos < e_end) {
-    const int k0 = __popc(__ballot_sync(kFull, my_end <= pos));
-    if (k0 == 32) {  // every row of the window ends at or before pos
+    // rows of the window with entries at or after pos that are not known matched
+    const unsigned open = __ballot_sync(kFull, my_end > pos) & ~mchd;
+    if (open == 0u) {  // the window is exhausted: continue after its last row
+      const int64_t win_end = __shfl_sync(kFull, my_end, 31);
+      if (win_end >= e_end) return;
+      if (win_end > pos) pos = win_end;
       wbase += 32;
-      my_end = row_end_or_max(P, wbase + 1 + lane);
+      const int64_t r = wbase + lane;
+      const bool in = r < (int64_t)P.n;
+      my_end = in ? __ldg(P.offsets + r + 1) : INT64_MAX;
+      my_st = in ? s.peek((uint32_t)r) : 0u;
+      mchd = __ballot_sync(kFull, !in || S::matched(my_st, (uint32_t)r));
       continue;
     }
-    const uint32_t x0 = (uint32_t)(wbase + k0);
-    const int64_t x0_end = __shfl_sync(kFull, my_end, k0);
-    // Row skip: a matched source row has nothing left to take.
-    uint32_t sx0 = 0;
-    if (lane == 0) sx0 = s.load(x0);
-    sx0 = __shfl_sync(kFull, sx0, 0);
-    if (S::matched(sx0)) {
-      pos = x0_end;
-      continue;
+    const int k1 = __ffs(open) - 1;
+    if (k1 > 0) {  // row k1 starts where row k1-1 ends
+      const int64_t st = __shfl_sync(kFull, my_end, k1 - 1);
+      if (st > pos) pos = st;
     }
+    if (pos >= e_end) return;
     const int64_t win_end = __shfl_sync(kFull, my_end, 31);
     const int64_t base = pos & ~(int64_t)3;
     int64_t cend = base + 128;
     if (cend > e_end) cend = e_end;
     if (cend > win_end) cend = win_end;
+    // chunk-relative 32-bit coordinates: entry base+p, p in [lo_r, hi_r)
+    const int lo_r = (int)(pos - base);
+    const int hi_r = (int)(cend - base);
+    const int64_t rel64 = my_end - base;
+    const int rel = rel64 < 0 ? -1 : (rel64 > 129 ? 129 : (int)rel64);
 
-    // neighbour ids: one aligned 128-bit load per lane
-    const int64_t e0 = base + 4 * (int64_t)lane;
+    // neighbour ids (one aligned 128-bit load per lane) and, in parallel, a
+    // fresh read of the head row's state
+    const int p0 = 4 * (int)lane;
+    const int64_t e0 = base + p0;
     uint32_t y[4] = {0u, 0u, 0u, 0u};
-    if (e0 < cend) {
+    if (p0 < hi_r) {
       if (e0 + 4 <= (int64_t)P.nnz) {
         const uint4 q = ld_stream_v4(P.nbrs + e0, pol_stream);
         y[0] = q.x; y[1] = q.y; y[2] = q.z; y[3] = q.w;
@@ -144,53 +169,52 @@ __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int
           if (e0 + j < (int64_t)P.nnz) y[j] = ld_stream(P.nbrs + e0 + j, pol_stream);
       }
     }
-    // row of each entry (window-relative), all lanes take part in the shuffles
+    const uint32_t x1 = (uint32_t)(wbase + k1);
+    uint32_t head = 0;
+    if (lane == 0) head = s.peek(x1);
+    head = __shfl_sync(kFull, head, 0);
+    if (S::matched(head, x1)) mchd |= 1u << k1;
+    if (lane == (unsigned)k1) my_st = head;
+
+    // row of each entry within the window
     int k[4];
-    k[0] = count_le(my_end, e0);
-    k[3] = count_le(my_end, e0 + 3);
+    k[0] = count_le(rel, p0);
+    k[3] = count_le(rel, p0 + 3);
     if (__any_sync(kFull, k[0] != k[3])) {
-      k[1] = count_le(my_end, e0 + 1);
-      k[2] = count_le(my_end, e0 + 2);
+      k[1] = count_le(rel, p0 + 1);
+      k[2] = count_le(rel, p0 + 2);
     } else {
       k[1] = k[0];
       k[2] = k[0];
     }
-    uint32_t valid = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (e0 + j >= pos && e0 + j < cend) valid |= 1u << j;
-
-    uint32_t xs[4], sx[4];
+    // words holding the row states, from the window snapshot
+    uint32_t rx[4], xs[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
+      rx[j] = __shfl_sync(kFull, my_st, k[j] & 31);
       xs[j] = (uint32_t)(wbase + k[j]);
-      sx[j] = 0;
     }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (valid >> j & 1u) {
-        if (j > 0 && k[j] == k[j - 1] && (valid >> (j - 1) & 1u))
-          sx[j] = sx[j - 1];
-        else
-          sx[j] = s.peek(xs[j]);
-      }
-    }
-    // filter: candidates have both endpoints unmatched (line 10 read)
-    uint32_t cand = 0;
-    uint32_t sy[4] = {0u, 0u, 0u, 0u};
+
+    // filter (the line-10 read): candidates have both endpoints unmatched
     bool want[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      want[j] = (valid >> j & 1u) && !S::matched(sx[j]) && y[j] != xs[j];
+      const int p = p0 + j;
+      want[j] = p >= lo_r && p < hi_r && !(mchd >> (k[j] & 31) & 1u) && !S::matched(rx[j], xs[j]) &&
+                y[j] != xs[j];
       if (want[j] && y[j] >= n32) {
         atomicOr(P.err, kErrBadId);
         want[j] = false;
       }
-      if (want[j]) sy[j] = s.peek(y[j]);
     }
+    uint32_t ry[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      if (want[j] && !S::matched(sy[j])) cand |= 1u << j;
+      if (want[j]) ry[j] = s.peek(y[j]);
+    uint32_t cand = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (want[j] && !S::matched(ry[j], y[j])) cand |= 1u << j;
 
     // resolve candidates: per row, one lane at a time
     for (;;) {
@@ -200,24 +224,24 @@ __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int
       const uint32_t key = have ? pick4(xs, j) : kNone;
       const unsigned peers = __match_any_sync(kFull, key);
       const int leader = __ffs(peers) - 1;
-      bool xm = false;
+      unsigned done = 0u;
       if (have && (int)lane == leader) {
         cand &= ~(1u << j);
-        xm = resolve_edge(s, key, pick4(y, j), P);
+        if (resolve_edge(s, key, pick4(y, j), pick4(rx, j), pick4(ry, j), P))
+          done = 1u << (key - (uint32_t)wbase);
       }
-      const bool row_done = __shfl_sync(kFull, xm, leader);
-      if (have && row_done) {
+      done = __reduce_or_sync(kFull, done);  // rows that are now matched
+      mchd |= done;
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj)
-          if (xs[jj] == key) cand &= ~(1u << jj);
-      }
+      for (int jj = 0; jj < 4; ++jj)
+        if (done >> (k[jj] & 31) & 1u) cand &= ~(1u << jj);
     }
     pos = cend;
   }
 }
 
 template <class S>
-__global__ void __launch_bounds__(512) sweep_kernel(SweepParams P) {
+__global__ void __launch_bounds__(512, 3) sweep_kernel(SweepParams P) {
   const unsigned lane = threadIdx.x & 31u;
   const S s(P);
   const uint64_t pol = policy_evict_first();
@@ -242,7 +266,7 @@ template <class S>
 __device__ __forceinline__ void serial_rows(const S& s, const SweepParams& P, uint64_t r0,
                                             uint64_t r1) {
   for (uint64_t x = r0; x < r1; ++x) {
-    if (S::matched(s.load((uint32_t)x))) continue;
+    if (S::matched(s.raw((uint32_t)x), (uint32_t)x)) continue;
     for (int64_t i = P.offsets[x]; i < P.offsets[x + 1]; ++i) {
       const uint32_t y = P.nbrs[i];
       if (y >= P.n) {
@@ -250,7 +274,7 @@ __device__ __forceinline__ void serial_rows(const S& s, const SweepParams& P, ui
         continue;
       }
       if (y == x) continue;
-      if (resolve_edge(s, (uint32_t)x, y, P)) break;
+      if (resolve_edge(s, (uint32_t)x, y, s.raw((uint32_t)x), s.raw(y), P)) break;
       if (ld_relaxed(P.err) & kErrTimeout) return;
     }
   }

@@ -192,7 +192,8 @@ def test_misaligned_and_bad_graphs(skp):
         skp.Graph(csr.offsets, bad)
     assert e.value.status == "MM_ERR_BAD_GRAPH"
     off = csr.offsets.clone()
-    off[4], off[5] = off[5], off[4]  # not monotone
+    a, b = int(off[4]), int(off[5])
+    off[4], off[5] = b, a            # not monotone
     with pytest.raises(skp.SkipperError) as e:
         skp.Graph(off, csr.nbrs)
     assert e.value.status == "MM_ERR_BAD_GRAPH"
