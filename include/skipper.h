@@ -241,6 +241,39 @@ mm_status mm_autotune_batched(mm_graph *g, uint64_t num_graphs, const int64_t *d
 /* Release the handle's scratch.  Does not touch the borrowed CSR. */
 mm_status mm_destroy(mm_graph *g);
 
+/*
+ * mm_skipper_static -- the same matching pass as mm_skipper, for callers that
+ * cannot allocate device memory while they run (a program whose device memory
+ * all belongs to its own pool after start-up, a serving loop that must not
+ * allocate per request, a plug-in inside a process whose allocator it does not
+ * own).  The paper has no counterpart to this call.
+ *
+ * No handle and no cudaMalloc: the pass keeps its scratch (one state byte per
+ * vertex, the merge-path partition table, the work counter and error word) in
+ * one fixed 8 MiB device array inside the library, which every GPU that loads
+ * the library holds until the process exits.  The caller passes the device CSR
+ * (same layout and alignment rules as mm_create_csr; it is not checked) and
+ * the mate array d_mate (uint32_t[n], written in full).
+ *
+ * Limits: n <= MM_STATIC_MAX_VERTICES (larger graphs return MM_ERR_ARG, with
+ * the reason in mm_last_error()); the grain is raised when needed so that the
+ * partition fits the fixed table.  Options: status_bits 0 or 8, serial, grain,
+ * block_threads, blocks_per_sm, spin_limit, poison_vertex; timing, use_graph,
+ * nosync and l2_persist give MM_ERR_UNSUPPORTED.  The call waits for its work
+ * and returns MM_OK, MM_ERR_TIMEOUT, MM_ERR_BAD_GRAPH, MM_ERR_ARG or
+ * MM_ERR_CUDA.
+ *
+ * The first call on a device looks up the array's device address on that
+ * device (make it before any stream capture).  All calls share the one array:
+ * each call clears what must start at zero, and calls whose work overlaps on
+ * the GPU (two host threads, two streams) race on it and must be serialised
+ * by the caller.
+ */
+#define MM_STATIC_MAX_VERTICES 7864064ull
+mm_status mm_skipper_static(uint64_t n, uint64_t nnz, const int64_t *d_offsets,
+                            const uint32_t *d_nbrs, uint32_t *d_mate, const mm_options *o,
+                            void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

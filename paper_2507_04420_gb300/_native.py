@@ -19,7 +19,7 @@ CSRC = os.path.join(_PKG, "csrc")
 INCLUDE = os.path.join(_ROOT, "include")
 LIB_DIR = os.path.join(_PKG, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libskipper.so")
-SOURCES = ["sweep.cu", "check.cu", "api.cu"]
+SOURCES = ["sweep.cu", "check.cu", "api.cu", "noalloc.cu"]
 HEADERS = ["state.cuh", "internal.h"]
 
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -137,6 +137,7 @@ SYMBOLS = [
     ("mm_timing_history", _I, [_P, ctypes.POINTER(Timing), _U32, ctypes.POINTER(_U32)]),
     ("mm_autotune_batched", _I, [_P, _U64, _P, _P, _P, ctypes.POINTER(Options), _P]),
     ("mm_destroy", _I, [_P]),
+    ("mm_skipper_static", _I, [_U64, _U64, _P, _P, _P, ctypes.POINTER(Options), _P]),
 ]
 
 STATUS = {0: "MM_OK", 1: "MM_ERR_ARG", 2: "MM_ERR_OOM", 3: "MM_ERR_CUDA", 4: "MM_ERR_TIMEOUT",

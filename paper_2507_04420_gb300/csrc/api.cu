@@ -53,6 +53,13 @@ struct BatchGraph {
 
 }  // namespace
 
+void skp::set_error_message(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
 struct mm_graph {
   int device = 0;
   int num_sms = 0;

@@ -19,6 +19,9 @@ void get_batched_kernels(bool word, bool serial, const void** prepare, const voi
 cudaError_t launch_graph_pairs(const uint32_t* mate, const int64_t* vbase, uint64_t num_graphs,
                                uint64_t n, uint64_t* graph_pairs, int grid, cudaStream_t s);
 
+// api.cu: message returned by mm_last_error() on this thread
+void set_error_message(const char* fmt, ...);
+
 // check.cu
 struct CheckScratch {
   unsigned long long* counters;  // mm_verdict-shaped device block (see check.cu)
