@@ -38,7 +38,7 @@ import torch
 __all__ = [
     "CSR", "Packed", "mix64", "rmat", "erdos_renyi", "uniform", "path", "star",
     "complete_bipartite", "grid", "disjoint_edges", "complete", "from_edges", "pack",
-    "batch_mix",
+    "batch_mix", "batch_packed", "unpack",
 ]
 
 _MASK64 = (1 << 64) - 1
@@ -383,3 +383,128 @@ def batch_mix(num_graphs: int, m_lo: float, m_hi: float, seed: int = 1, device="
             side = max(2, int(round(math.sqrt(m / 2))))
             out.append(grid(side, side, device))
     return out
+
+
+def unpack(packed: Packed, g: int) -> CSR:
+    """Graph g of a block-diagonal packing as a standalone CSR with local ids."""
+    v0, v1 = int(packed.vbase[g]), int(packed.vbase[g + 1])
+    e0, e1 = int(packed.ebase[g]), int(packed.ebase[g + 1])
+    off = packed.csr.offsets[v0:v1 + 1] - e0
+    nb = packed.csr.nbrs[e0:e1] - v0
+    return CSR(off.contiguous(), nb.contiguous())
+
+
+def _scramble(x: torch.Tensor, bits: torch.Tensor, a1: torch.Tensor, a2: torch.Tensor) -> torch.Tensor:
+    """A bijection of [0, 2**bits) per element: odd multiply, xor-shift, odd multiply (mod 2**bits)."""
+    mask = (torch.ones_like(bits) << bits) - 1
+    x = (x * a1) & mask
+    x = x ^ (x >> ((bits + 1) // 2))
+    return (x * a2) & mask
+
+
+def batch_packed(num_graphs: int, m_lo: float, m_hi: float, seed: int = 1, device="cpu",
+                 chunks: int = 1, kinds=("er", "rmat", "grid")):
+    """A packed batch of num_graphs graphs drawn in one vectorised pass.
+
+    Edge counts are log-uniform in [m_lo, m_hi]; graph g is kinds[g % len(kinds)]:
+    ER (n = 2m/ef, m uniform endpoint draws), R-MAT (edge factor ef uniform in 8..32,
+    n = 2**round(log2(m/ef)), a/b/c/d = .57/.19/.19/.05, ids scrambled by a per-graph
+    bijection) or a side x side grid (side = round(sqrt(m/2))).  Loops and repeats are
+    dropped.  Returns (Packed, kinds list)."""
+    G = num_graphs
+    h = _draw(seed, 8, 0, 3 * G, "cpu")
+    uni = (_lsr(h, 11).to(torch.float64) / float(1 << 53)).tolist()
+    ms, ns, kind_of, efs, scales, sides = [], [], [], [], [], []
+    for g in range(G):
+        m = int(round(math.exp(math.log(m_lo) + uni[3 * g] * (math.log(m_hi) - math.log(m_lo)))))
+        k = kinds[g % len(kinds)]
+        ef = 8 + int(uni[3 * g + 1] * 25) % 25
+        sc = side = 0
+        if k == "er":
+            n = max(16, int(round(2 * m / ef)))
+        elif k == "rmat":
+            sc = max(4, int(round(math.log2(max(m / ef, 16)))))
+            n = 1 << sc
+        else:
+            side = max(2, int(round(math.sqrt(m / 2))))
+            n = side * side
+        ms.append(m); ns.append(n); kind_of.append(k); efs.append(ef); scales.append(sc); sides.append(side)
+    vbase = torch.zeros(G + 1, dtype=torch.int64)
+    vbase[1:] = torch.cumsum(torch.tensor(ns, dtype=torch.int64), 0)
+    N = int(vbase[-1])
+    if N >= 2**31:
+        raise ValueError("packed vertex count must stay below 2**31")
+    vb = vbase.to(device)
+    us, vs = [], []
+
+    def per_edge(ids, counts):
+        return torch.repeat_interleave(torch.tensor(ids, dtype=torch.int64, device=device),
+                                       torch.tensor(counts, dtype=torch.int64, device=device))
+
+    # Erdos-Renyi members
+    er = [g for g in range(G) if kind_of[g] == "er"]
+    if er:
+        ge = per_edge(er, [ms[g] for g in er])
+        nn = torch.tensor(ns, dtype=torch.int64, device=device)[ge]
+        cnt = ge.numel()
+        u = (_draw(seed, 20, 0, cnt, device) & 0x7FFFFFFFFFFFFFFF) % nn
+        v = (_draw(seed, 21, 0, cnt, device) & 0x7FFFFFFFFFFFFFFF) % nn
+        us.append(u + vb[ge]); vs.append(v + vb[ge])
+    # R-MAT members
+    rm = [g for g in range(G) if kind_of[g] == "rmat"]
+    if rm:
+        ge = per_edge(rm, [ms[g] for g in rm])
+        cnt = ge.numel()
+        sc_all = torch.tensor(scales, dtype=torch.int64, device=device)
+        s_e = sc_all[ge]
+        smax = int(max(scales[g] for g in rm))
+        u = torch.zeros(cnt, dtype=torch.int64, device=device)
+        v = torch.zeros(cnt, dtype=torch.int64, device=device)
+        ta, tb, tc = int(0.57 * 2**32), int(0.76 * 2**32), int(0.95 * 2**32)
+        per = (smax + 1) // 2
+        ctr = torch.arange(cnt, dtype=torch.int64, device=device) * per
+        hh = None
+        for lvl in range(smax):
+            if lvl % 2 == 0:
+                hh = mix64(ctr + lvl // 2 + _base(seed, 22))
+                r = hh & 0xFFFFFFFF
+            else:
+                r = _lsr(hh, 32)
+            u = (u << 1) | (r >= tb).to(torch.int64)
+            v = (v << 1) | (((r >= ta) & (r < tb)) | (r >= tc)).to(torch.int64)
+        u = u >> (smax - s_e)
+        v = v >> (smax - s_e)
+        gconst = torch.tensor([_py_mix64(seed * 7919 + g) & 0xFFFFFFFF for g in range(G)],
+                              dtype=torch.int64, device=device)
+        a1 = (gconst[ge] << 1) | 1
+        a2 = ((gconst[ge] >> 7) << 1) | 1
+        u = _scramble(u, s_e, a1, a2)
+        v = _scramble(v, s_e, a1, a2)
+        us.append(u + vb[ge]); vs.append(v + vb[ge])
+    # grid members
+    gr = [g for g in range(G) if kind_of[g] == "grid"]
+    if gr:
+        for horiz in (True, False):
+            cnts = [sides[g] * (sides[g] - 1) for g in gr]
+            ge = per_edge(gr, cnts)
+            side = torch.tensor(sides, dtype=torch.int64, device=device)[ge]
+            first = torch.zeros(len(gr) + 1, dtype=torch.int64)
+            first[1:] = torch.cumsum(torch.tensor(cnts, dtype=torch.int64), 0)
+            local = torch.arange(ge.numel(), dtype=torch.int64, device=device) - \
+                first.to(device)[:-1].repeat_interleave(torch.tensor(cnts, device=device))
+            if horiz:   # (r, c) - (r, c+1)
+                r, c = local // (side - 1), local % (side - 1)
+                a = r * side + c
+                b = a + 1
+            else:       # (r, c) - (r+1, c)
+                r, c = local // side, local % side
+                a = r * side + c
+                b = a + side
+            us.append(a + vb[ge]); vs.append(b + vb[ge])
+    u = torch.cat(us)
+    v = torch.cat(vs)
+    keep = u != v
+    u, v = u[keep].to(torch.int32), v[keep].to(torch.int32)
+    csr = _csr_from_directed_pairs(N, u, v, max(1, chunks))
+    ebase = csr.offsets[vb]
+    return Packed(csr, vb, ebase), kind_of

@@ -238,6 +238,48 @@ mm_status mm_autotune_batched(mm_graph *g, uint64_t num_graphs, const int64_t *d
                               const int64_t *d_ebase, uint32_t *d_mate_scratch,
                               mm_options *o, void *cuda_stream);
 
+/*
+ * Many independent graphs, each in its own device buffers, in one persistent
+ * launch -- the form a request server uses: requests keep their CSR resident
+ * where it was copied, and every graph admitted since the last launch is
+ * matched together (no repacking).  Each graph is split into merge-path units
+ * of `grain` rows + entries like a single graph (Section IV-C's equal-edge
+ * blocks); the units of all graphs are handed out from one counter.
+ *
+ * mm_graph_desc: n, nnz, offsets int64_t[n+1], nbrs uint32_t[nnz] (16-byte
+ * aligned) and mate uint32_t[n], all in device memory and owned by the
+ * caller; with status_bits 32 mate is also the graph's state array, with 8
+ * the handle keeps one state byte per vertex for all graphs.
+ *
+ * mm_multi_create: a handle that owns the device tables, partition, state
+ * pool, checker counters and control words; it grows them (cudaMalloc) only
+ * when a call needs more than any earlier call.  Calls on one handle must be
+ * ordered (one stream, or synchronised by the caller).
+ * mm_skipper_multi: options as mm_skipper (status_bits, serial -- one thread
+ * per graph in SGMM order --, grain, block_threads, blocks_per_sm, spin_limit,
+ * nosync); timing, use_graph, poison_vertex and l2_persist give
+ * MM_ERR_UNSUPPORTED.  Waits for the GPU unless nosync (then mm_multi_sync).
+ * mm_validate_multi: the exact checker (counting rules above, without a pair
+ * list) for every graph at once; h_out[k] is graph k's verdict.  Synchronous.
+ */
+typedef struct mm_graph_desc {
+    uint64_t n;
+    uint64_t nnz;
+    const int64_t *offsets;
+    const uint32_t *nbrs;
+    uint32_t *mate;
+} mm_graph_desc;
+
+typedef struct mm_multi mm_multi;
+
+mm_status mm_multi_create(mm_multi **out);
+mm_status mm_skipper_multi(mm_multi *m, uint64_t num_graphs, const mm_graph_desc *h_descs,
+                           const mm_options *o, void *cuda_stream);
+mm_status mm_multi_sync(mm_multi *m, void *cuda_stream);
+mm_status mm_validate_multi(mm_multi *m, uint64_t num_graphs, const mm_graph_desc *h_descs,
+                            mm_verdict *h_out, void *cuda_stream);
+mm_status mm_multi_destroy(mm_multi *m);
+
 /* Release the handle's scratch.  Does not touch the borrowed CSR. */
 mm_status mm_destroy(mm_graph *g);
 

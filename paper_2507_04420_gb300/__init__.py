@@ -18,9 +18,9 @@ from typing import Optional
 import torch
 
 from . import _native
-from ._native import Options, Timing, Verdict
+from ._native import GraphDesc, Options, Timing, Verdict
 
-__all__ = ["Graph", "HostSession", "SkipperError", "match", "validate", "Options", "Verdict", "Timing",
+__all__ = ["Graph", "HostSession", "Multi", "SkipperError", "match", "validate", "Options", "Verdict", "Timing",
            "UNMATCHED", "lib", "options"]
 
 UNMATCHED = 0xFFFFFFFF
@@ -202,6 +202,60 @@ def validate(offsets: torch.Tensor, nbrs: torch.Tensor, mate: torch.Tensor, pair
         return g.validate(mate, pairs)
 
 
+class Multi:
+    """Many independent graphs, each in its own device tensors, matched in one
+    launch (mm_skipper_multi) and checked in one launch (mm_validate_multi).
+
+    A graph is a tuple (offsets int64[n+1], nbrs int32[nnz], mate int32[n]) of
+    CUDA tensors; calls on one Multi must be ordered (one stream)."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check(lib.mm_multi_create(ctypes.byref(h)), "mm_multi_create")
+        self._h = h
+
+    @staticmethod
+    def _descs(graphs):
+        arr = (GraphDesc * max(1, len(graphs)))()
+        for i, (off, nb, mate) in enumerate(graphs):
+            _need(off, "offsets", (torch.int64,))
+            _need(nb, "nbrs", _U32)
+            _need(mate, "mate", _U32)
+            arr[i].n = off.numel() - 1
+            arr[i].nnz = nb.numel()
+            arr[i].offsets = off.data_ptr()
+            arr[i].nbrs = nb.data_ptr() if nb.numel() else None
+            arr[i].mate = mate.data_ptr() if mate.numel() else None
+        return arr
+
+    def run(self, graphs, stream=None, opts: Optional[Options] = None, **kw):
+        o = opts if opts is not None else options(**kw)
+        arr = self._descs(graphs)
+        _check(lib.mm_skipper_multi(self._h, len(graphs), arr, ctypes.byref(o), _stream_ptr(stream)),
+               "mm_skipper_multi")
+
+    def sync(self, stream=None):
+        _check(lib.mm_multi_sync(self._h, _stream_ptr(stream)), "mm_multi_sync")
+
+    def validate(self, graphs, stream=None):
+        arr = self._descs(graphs)
+        out = (Verdict * max(1, len(graphs)))()
+        _check(lib.mm_validate_multi(self._h, len(graphs), arr, out, _stream_ptr(stream)),
+               "mm_validate_multi")
+        return [out[i] for i in range(len(graphs))]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.mm_multi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class HostSession:
     """Skipper on graphs that live in host memory.
 
@@ -228,6 +282,7 @@ class HostSession:
         key = (n, nnz)
         g = self._graphs.get(key)
         if g is None:  # the handle only borrows the buffers; their contents change per run
+            self.close()
             g = self._graphs[key] = Graph(off_d, nb_d, check=False, stream=stream)
         g.skipper(mate=mate_d, stream=stream, **kw)
         if mate_out is None:

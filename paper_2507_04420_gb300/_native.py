@@ -19,8 +19,8 @@ CSRC = os.path.join(_PKG, "csrc")
 INCLUDE = os.path.join(_ROOT, "include")
 LIB_DIR = os.path.join(_PKG, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libskipper.so")
-SOURCES = ["sweep.cu", "check.cu", "api.cu", "noalloc.cu"]
-HEADERS = ["state.cuh", "internal.h"]
+SOURCES = ["sweep.cu", "check.cu", "api.cu", "noalloc.cu", "multi.cu"]
+HEADERS = ["state.cuh", "internal.h", "walk.cuh"]
 
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
@@ -101,6 +101,16 @@ class Timing(ctypes.Structure):
     ]
 
 
+class GraphDesc(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_uint64),
+        ("nnz", ctypes.c_uint64),
+        ("offsets", ctypes.c_void_p),
+        ("nbrs", ctypes.c_void_p),
+        ("mate", ctypes.c_void_p),
+    ]
+
+
 class Verdict(ctypes.Structure):
     _fields_ = [
         ("flags", ctypes.c_uint32),
@@ -136,6 +146,11 @@ SYMBOLS = [
     ("mm_get_timing", _I, [_P, ctypes.POINTER(Timing)]),
     ("mm_timing_history", _I, [_P, ctypes.POINTER(Timing), _U32, ctypes.POINTER(_U32)]),
     ("mm_autotune_batched", _I, [_P, _U64, _P, _P, _P, ctypes.POINTER(Options), _P]),
+    ("mm_multi_create", _I, [ctypes.POINTER(_P)]),
+    ("mm_skipper_multi", _I, [_P, _U64, ctypes.POINTER(GraphDesc), ctypes.POINTER(Options), _P]),
+    ("mm_multi_sync", _I, [_P, _P]),
+    ("mm_validate_multi", _I, [_P, _U64, ctypes.POINTER(GraphDesc), ctypes.POINTER(Verdict), _P]),
+    ("mm_multi_destroy", _I, [_P]),
     ("mm_destroy", _I, [_P]),
     ("mm_skipper_static", _I, [_U64, _U64, _P, _P, _P, ctypes.POINTER(Options), _P]),
 ]

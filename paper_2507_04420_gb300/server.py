@@ -1,0 +1,223 @@
+"""Continuous-batching Skipper server on one GPU.
+
+Requests (graphs in host memory) arrive at any time.  A worker thread admits
+them in arrival order while their device footprint fits the memory budget,
+copies each CSR to its own device buffers on a copy stream (the CSR and the
+state stay resident until the request completes), and whenever a compute slot
+is free launches one multi-graph pass (mm_skipper_multi) over every request
+admitted since the last launch.  Two compute slots alternate, so a new batch
+is admitted, copied and launched while the previous one is still on the GPU.
+Each result is checked by the exact device checker (mm_validate_multi) before
+its request completes; its mate array is copied back on a second copy stream.
+
+Latency of a request = completion (mate in host memory, verdict known) minus
+submission.
+"""
+from __future__ import annotations
+
+import collections
+import queue
+import threading
+import time
+from typing import List, Optional, Sequence, Tuple
+
+import torch
+
+from . import Multi, SkipperError, options
+
+__all__ = ["Request", "Server", "device_bytes", "plan_admission"]
+
+
+def device_bytes(n: int, nnz: int) -> int:
+    """Device memory a request holds while resident: offsets, neighbour ids,
+    mate/state, rounded up to the allocator's 512-byte granules."""
+    r = lambda b: (b + 511) // 512 * 512
+    return r(8 * (n + 1)) + r(4 * max(nnz, 1)) + r(4 * max(n, 1))
+
+
+def plan_admission(sizes: Sequence[int], used: int, budget: int, max_graphs: int) -> Tuple[int, int]:
+    """How many of the pending requests (sizes in bytes, arrival order) to admit.
+
+    Admission is in arrival order and stops at the first request that does not
+    fit (no overtaking, so no request starves).  Returns (count, bytes)."""
+    k = 0
+    add = 0
+    for s in sizes:
+        if k >= max_graphs or used + add + s > budget:
+            break
+        add += s
+        k += 1
+    return k, add
+
+
+class Request:
+    __slots__ = ("rid", "offsets", "nbrs", "n", "nnz", "arrival", "done_t", "mate", "verdict",
+                 "error", "_event", "_dev", "_bytes", "tick")
+
+    def __init__(self, rid: int, offsets: torch.Tensor, nbrs: torch.Tensor):
+        self.rid = rid
+        self.offsets, self.nbrs = offsets, nbrs
+        self.n, self.nnz = offsets.numel() - 1, nbrs.numel()
+        self.arrival = time.perf_counter()
+        self.done_t = None
+        self.mate = None
+        self.verdict = None
+        self.error = None
+        self._event = threading.Event()
+        self._dev = None
+        self._bytes = device_bytes(self.n, self.nnz)
+        self.tick = None
+
+    def wait(self, timeout: Optional[float] = None) -> bool:
+        return self._event.wait(timeout)
+
+    @property
+    def latency(self) -> Optional[float]:
+        return None if self.done_t is None else self.done_t - self.arrival
+
+
+class Server:
+    def __init__(self, device=None, memory_bytes: Optional[int] = None, reserve_bytes: int = 2 << 30,
+                 max_graphs_per_tick: int = 4096, status_bits: int = 32, grain: int = 2048,
+                 serial: bool = False, validate: bool = True, slots: int = 2):
+        self.dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        free, _ = torch.cuda.mem_get_info(self.dev)
+        self.budget = memory_bytes if memory_bytes is not None else max(0, free - reserve_bytes)
+        self.max_graphs = max_graphs_per_tick
+        self.validate = validate
+        self.opts = options(status_bits=status_bits, grain=grain, serial=int(serial), nosync=1)
+        self.h2d = torch.cuda.Stream(self.dev)
+        self.d2h = torch.cuda.Stream(self.dev)
+        self.slots = [(torch.cuda.Stream(self.dev), Multi()) for _ in range(slots)]
+        self._next_slot = 0
+        self._inbox: "queue.Queue[Request]" = queue.Queue()
+        self._rid = 0
+        self._lock = threading.Lock()
+        self._closing = False
+        self.used = 0
+        self.ticks = 0
+        self.tick_sizes: List[int] = []
+        self.error: Optional[BaseException] = None
+        self._thread = threading.Thread(target=self._run, name="skipper-server", daemon=True)
+        self._thread.start()
+
+    # -- client side ------------------------------------------------------------
+    def submit(self, offsets: torch.Tensor, nbrs: torch.Tensor) -> Request:
+        """Queue one graph (host CSR; pinned memory makes the copy asynchronous)."""
+        if offsets.is_cuda or nbrs.is_cuda:
+            raise ValueError("submit host tensors")
+        with self._lock:
+            rid = self._rid
+            self._rid += 1
+        req = Request(rid, offsets, nbrs)
+        if req._bytes > self.budget:
+            req.error = MemoryError(f"request needs {req._bytes} device bytes, budget {self.budget}")
+            req.done_t = time.perf_counter()
+            req._event.set()
+            return req
+        self._inbox.put(req)
+        return req
+
+    def close(self, timeout: float = 600.0):
+        self._closing = True
+        self._thread.join(timeout)
+        for _, m in self.slots:
+            m.close()
+        if self.error is not None:
+            raise self.error
+
+    # -- worker -------------------------------------------------------------------
+    def _admit(self, req: Request):
+        with torch.cuda.stream(self.h2d):
+            off = torch.empty(req.n + 1, dtype=torch.int64, device=self.dev)
+            nb = torch.empty(max(req.nnz, 1), dtype=torch.int32, device=self.dev)[: req.nnz]
+            mate = torch.empty(req.n, dtype=torch.int32, device=self.dev)
+            off.copy_(req.offsets, non_blocking=True)
+            if req.nnz:
+                nb.copy_(req.nbrs, non_blocking=True)
+        req._dev = (off, nb, mate)
+
+    def _launch(self, batch: List[Request]):
+        stream, multi = self.slots[self._next_slot]
+        slot = self._next_slot
+        self._next_slot = (self._next_slot + 1) % len(self.slots)
+        copied = torch.cuda.Event()
+        copied.record(self.h2d)
+        stream.wait_event(copied)
+        graphs = [r._dev for r in batch]
+        multi.run(graphs, stream=stream, opts=self.opts)
+        swept = torch.cuda.Event()
+        swept.record(stream)
+        for r in batch:  # the device tensors were made on the copy stream; they are used here too
+            for t in r._dev:
+                t.record_stream(stream)
+        self.d2h.wait_event(swept)
+        with torch.cuda.stream(self.d2h):
+            for r in batch:
+                r.mate = torch.empty(r.n, dtype=torch.int32, pin_memory=True)
+                r.mate.copy_(r._dev[2], non_blocking=True)
+                r._dev[2].record_stream(self.d2h)
+        back = torch.cuda.Event()
+        back.record(self.d2h)
+        self.ticks += 1
+        self.tick_sizes.append(len(batch))
+        return (slot, batch, back)
+
+    def _complete(self, tick) -> bool:
+        slot, batch, back = tick
+        if not back.query():
+            return False
+        stream, multi = self.slots[slot]
+        err = None
+        try:
+            multi.sync(stream)  # the pass's own status (timeouts, bad ids)
+        except SkipperError as e:
+            err = e
+        verdicts = multi.validate([r._dev for r in batch], stream=stream) if (self.validate and err is None) else None
+        now = time.perf_counter()
+        for i, r in enumerate(batch):
+            r.verdict = None if verdicts is None else verdicts[i]
+            r.error = err
+            r.done_t = now
+            r._dev = None
+            self.used -= r._bytes
+            r._event.set()
+        return True
+
+    def _run(self):
+        pending: "collections.deque[Request]" = collections.deque()
+        staged: List[Request] = []
+        inflight: "collections.deque" = collections.deque()
+        torch.cuda.set_device(self.dev)
+        try:
+            while True:
+                busy = False
+                while True:
+                    try:
+                        pending.append(self._inbox.get_nowait())
+                    except queue.Empty:
+                        break
+                while inflight and self._complete(inflight[0]):
+                    inflight.popleft()
+                    busy = True
+                k, add = plan_admission([r._bytes for r in pending], self.used, self.budget,
+                                        self.max_graphs - len(staged))
+                for _ in range(k):
+                    r = pending.popleft()
+                    self._admit(r)
+                    staged.append(r)
+                    busy = True
+                self.used += add
+                if staged and len(inflight) < len(self.slots):
+                    inflight.append(self._launch(staged))
+                    staged = []
+                    busy = True
+                if self._closing and not pending and not staged and not inflight and self._inbox.empty():
+                    return
+                if not busy:
+                    time.sleep(50e-6)
+        except BaseException as e:  # surface worker failures to close() and to waiters
+            self.error = e
+            for r in list(pending) + staged + [r for t in inflight for r in t[1]]:
+                r.error = e
+                r._event.set()

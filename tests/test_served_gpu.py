@@ -1,0 +1,132 @@
+"""Multi-graph launches and the continuous-batching server against the oracle.
+
+The server matches whatever requests have arrived in one launch while earlier
+ones may still be on the GPU.  A request's result must not depend on its
+company: in serial mode (one thread per graph, SGMM order) the mate array must
+equal the graph's matching computed alone byte for byte; in parallel mode each
+result must be a maximal matching that the oracle and the device checker both
+accept with identical verdicts.
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+import oracle
+from tests.conftest import cuda_ok
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not cuda_ok(), reason="needs a CUDA GPU")]
+
+
+@pytest.fixture(scope="module")
+def skp():
+    import paper_2507_04420_gb300 as m
+    torch.cuda.set_device(0)
+    return m
+
+
+@pytest.fixture(scope="module")
+def graphs():
+    gs = gg.batch_mix(24, 1e2, 5e4, seed=31)
+    gs.append(gg.CSR(torch.zeros(4, dtype=torch.int64), torch.zeros(0, dtype=torch.int32)))  # no edges
+    gs.append(gg.star(3000))
+    return gs
+
+
+def _np(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+@pytest.mark.parametrize("bits", [8, 32])
+def test_multi_serial_equals_sgmm_and_parallel_valid(skp, graphs, bits):
+    dev = [g.to("cuda") for g in graphs]
+    m = skp.Multi()
+    try:
+        mates = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in graphs]
+        tri = [(d.offsets, d.nbrs, mt) for d, mt in zip(dev, mates)]
+        m.run(tri, serial=1, status_bits=bits)
+        for g, mt in zip(graphs, mates):
+            ref, _ = oracle.sgmm(g.offsets.numpy(), g.nbrs.numpy())
+            assert np.array_equal(_np(mt), ref)
+        for grain in (128, 2048):
+            m.run(tri, status_bits=bits, grain=grain)
+            verdicts = m.validate(tri)
+            for g, mt, vd in zip(graphs, mates, verdicts):
+                vr = oracle.check(g.offsets.numpy(), g.nbrs.numpy(), _np(mt))
+                assert vr.flags == 0 and vd.as_dict() == vr.as_dict()
+    finally:
+        m.close()
+
+
+def test_multi_validate_reports_corruption_per_graph(skp, graphs):
+    dev = [g.to("cuda") for g in graphs[:6]]
+    m = skp.Multi()
+    try:
+        mates = [torch.empty(d.n, dtype=torch.int32, device="cuda") for d in dev]
+        tri = [(d.offsets, d.nbrs, mt) for d, mt in zip(dev, mates)]
+        m.run(tri)
+        mates[3][:] = -1                      # graph 3 left unmatched
+        verdicts = m.validate(tri)
+        for k, (g, mt, vd) in enumerate(zip(graphs[:6], mates, verdicts)):
+            vr = oracle.check(g.offsets.numpy(), g.nbrs.numpy(), _np(mt))
+            assert vd.as_dict() == vr.as_dict()
+            assert (vr.flags != 0) == (k == 3 and g.nnz > 0)
+    finally:
+        m.close()
+
+
+def _pinned(g):
+    return g.offsets.pin_memory(), g.nbrs.pin_memory()
+
+
+@pytest.mark.parametrize("serial", [1, 0])
+def test_server_results_same_alone_and_in_the_mix(skp, graphs, serial):
+    from paper_2507_04420_gb300.server import Server
+    alone = []
+    for g in graphs:
+        d = g.to("cuda")
+        with skp.Graph(d.offsets, d.nbrs) as h:
+            alone.append(_np(h.skipper(serial=serial, status_bits=32)))
+    # a small memory budget forces several admission rounds, and staggered
+    # submissions make requests join while earlier ones are on the GPU
+    budget = max(4 * 1024 * 1024, 3 * max(g.nnz * 4 + g.n * 12 for g in graphs))
+    srv = Server(memory_bytes=budget, serial=bool(serial), status_bits=32)
+    reqs = []
+
+    def client():
+        for rep in range(3):
+            for g in graphs:
+                reqs.append((g, srv.submit(*_pinned(g))))
+                if len(reqs) % 7 == 0:
+                    time.sleep(0.002)
+
+    t = threading.Thread(target=client)
+    t.start()
+    t.join()
+    for _, r in reqs:
+        assert r.wait(120)
+    srv.close()
+    assert srv.ticks > 1
+    for idx, (g, r) in enumerate(reqs):
+        assert r.error is None
+        m = r.mate.numpy().view(np.uint32)
+        vr = oracle.check(g.offsets.numpy(), g.nbrs.numpy(), m)
+        assert vr.flags == 0 and r.verdict.as_dict() == vr.as_dict()
+        if serial:
+            assert np.array_equal(m, alone[idx % len(graphs)])
+        assert r.latency is not None and r.latency > 0
+
+
+def test_server_rejects_what_can_never_fit(skp):
+    from paper_2507_04420_gb300.server import Server
+    srv = Server(memory_bytes=1 << 20)
+    g = gg.rmat(14, 16, seed=2)
+    r = srv.submit(*_pinned(g))
+    assert r.wait(5) and isinstance(r.error, MemoryError)
+    small = gg.path(100)
+    r2 = srv.submit(*_pinned(small))
+    assert r2.wait(60) and r2.error is None and r2.verdict.flags == 0
+    srv.close()
