@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--scale", type=int, default=27)
     ap.add_argument("--edge-factor", type=int, default=16)
     ap.add_argument("--seed", type=int, default=1)
-    ap.add_argument("--bits", type=int, default=8, choices=[8, 32])
+    ap.add_argument("--bits", type=int, default=8, choices=[2, 8, 32])
     ap.add_argument("--grain", type=int, default=8192)
     ap.add_argument("--block", type=int, default=512)
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -63,6 +63,12 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--batch-reps", type=int, default=20)
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--served-rate", type=float, default=2000.0, help="Poisson arrivals per second")
+    ap.add_argument("--served-seconds", type=float, default=4.0)
+    ap.add_argument("--served-pool", type=int, default=16)
+    ap.add_argument("--served-min-edges", type=float, default=1e4)
+    ap.add_argument("--served-max-edges", type=float, default=2e8)
     return ap.parse_args()
 
 
@@ -317,6 +323,93 @@ def run_batched(args, skp):
 
 
 # ----------------------------------------------------------------------------
+# served: Poisson request stream through the continuous-batching server
+# ----------------------------------------------------------------------------
+def run_served(args, skp):
+    import math
+    import numpy as np
+    import torch
+    import graphgen as gg
+    from paper_2507_04420_gb300.server import Server
+    t = time.time()
+    P = args.served_pool
+    lo, hi = math.log(args.served_min_edges), math.log(args.served_max_edges)
+    pool = []
+    for i in range(P):   # stratified log-uniform sizes, R-MAT and uniform graphs in turn
+        m = int(math.exp(lo + (i + 0.5) / P * (hi - lo)))
+        if i % 2 == 0:
+            scale = max(4, int(round(math.log2(max(m / 16, 16)))))
+            g = gg.rmat(scale, max(1, m >> scale), seed=args.seed + 300 + i, device="cuda")
+        else:
+            g = gg.uniform(max(16, m // 8), m, seed=args.seed + 300 + i, device="cuda")
+        pool.append((g.offsets.cpu().pin_memory(), g.nbrs.cpu().pin_memory(), g.n, g.nnz))
+        del g
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(args.seed + 400)
+    gaps = rng.exponential(1.0 / args.served_rate, size=int(args.served_rate * args.served_seconds * 2) + 16)
+    times = np.cumsum(gaps)
+    times = times[times < args.served_seconds]
+    picks = rng.integers(0, P, size=times.size)
+    entries = int(sum(pool[p][3] for p in picks))
+    log(f"served: pool of {P} graphs ({sum(x[3] for x in pool)} entries) in {time.time() - t:.1f}s; "
+        f"{times.size} requests over {args.served_seconds}s")
+    out = {"workload": f"Poisson arrivals {args.served_rate:g}/s for {args.served_seconds:g}s; each request "
+                       f"one of {P} pre-generated graphs (R-MAT / uniform in turn, undirected edges "
+                       f"log-uniform in [{args.served_min_edges:g}, {args.served_max_edges:g}]) held in "
+                       "pinned host memory", "requests": int(times.size), "entries": entries}
+
+    def run_trace(submit, finish):
+        t0 = time.perf_counter()
+        for tt, p in zip(times, picks):
+            now = time.perf_counter() - t0
+            if tt > now:
+                time.sleep(tt - now)
+            submit(p, t0 + tt)
+        return t0, finish()
+
+    srv = Server(status_bits=args.bits, grain=2048)
+    reqs = []
+    t0, _ = run_trace(lambda p, at: reqs.append(srv.submit(pool[p][0], pool[p][1])),
+                      lambda: [r.wait(600) for r in reqs])
+    srv.close()   # raises the worker's error, if any
+    if any(r.done_t is None for r in reqs):
+        raise SystemExit("served: requests did not complete")
+    bad = sum(1 for r in reqs if r.error is not None or r.verdict is None or r.verdict.flags != 0)
+    lat = [r.latency * 1e3 for r in reqs]
+    end = max(r.done_t for r in reqs)
+    out["served"] = {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+                     "gedges_s": entries / (end - t0) / 1e9, "launches": srv.ticks,
+                     "mean_graphs_per_launch": statistics.mean(srv.tick_sizes), "invalid": bad,
+                     "how": "server.Server: admission by device-memory budget, H2D on a copy stream, "
+                            "one mm_skipper_multi launch per tick on two alternating compute streams, "
+                            "mm_validate_multi before completion, D2H on a second copy stream"}
+    # serial plain: one request at a time through the plain API, in arrival order
+    sess = skp.HostSession(max(x[2] for x in pool), max(x[3] for x in pool))
+    lat2 = []
+    bad2 = 0
+    mates = {}
+
+    def serial_submit(p, at):
+        nonlocal bad2
+        off, nb, n, _ = pool[p]
+        if p not in mates:
+            mates[p] = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        sess.run(off, nb, mates[p], check=True, status_bits=args.bits, grain=2048)
+        bad2 += sess.last_verdict.flags != 0
+        lat2.append((time.perf_counter() - at) * 1e3)
+
+    t0, _ = run_trace(serial_submit, lambda: None)
+    end2 = time.perf_counter()
+    sess.close()
+    out["serial_plain"] = {"p50_ms": pct(lat2, 50), "p99_ms": pct(lat2, 99),
+                           "gedges_s": entries / (end2 - t0) / 1e9, "invalid": bad2,
+                           "how": "HostSession.run per request: H2D, mm_create_csr when the size "
+                                  "changes, mm_skipper, mm_validate, D2H, synchronous"}
+    out["throughput_vs_serial"] = out["served"]["gedges_s"] / out["serial_plain"]["gedges_s"]
+    return out
+
+
+# ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
 def run_ours(args):
@@ -386,8 +479,8 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     sweep_bytes = 8 * (n + 1) + 4 * nnz
     achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9
-    s = 1 if args.bits == 8 else 4
-    step_bytes = 8 * (n + 1) + 4 * nnz + s * n + (4 * n if args.bits == 8 else 0)
+    s = {2: 0.25, 8: 1.0, 32: 4.0}[args.bits]   # state bytes per vertex
+    step_bytes = int(8 * (n + 1) + 4 * nnz + s * n + (4 * n if args.bits != 32 else 0))
     traffic = ncu_traffic(cfg["workload"], args.bits)
 
     # end to end through the public API with host buffers
@@ -430,22 +523,27 @@ def run_ours(args):
                          f"in {cs['seconds']:.2f}s"}
 
     batched = None
+    h.close()
+    del g, h_off, h_nb
+    torch.cuda.empty_cache()
     if not args.no_batched:
-        h.close()
-        del g, h_off, h_nb
-        torch.cuda.empty_cache()
         batched = run_batched(args, skp)
+
+    served = None
+    if not args.no_served:
+        torch.cuda.empty_cache()
+        served = run_served(args, skp)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u8" if args.bits == 8 else "u32", "data": "synthetic",
+        "vs_baseline": None, "dtype": {2: "u2", 8: "u8", 32: "u32"}[args.bits], "data": "synthetic",
         "config": dict(cfg, status_bits=args.bits, grain=args.grain, block_threads=args.block,
                        parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
                        l2="inputs larger than L2 (CSR %.1f GB vs 129 MB L2); no flush" % (sweep_bytes / 1e9)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": f"sweep_kernel<{'Byte' if args.bits == 8 else 'Word'}State>",
+                     "kernel": f"sweep_kernel<{ {2: 'TwoBit', 8: 'Byte', 32: 'Word'}[args.bits]}State>",
                      "bytes_per_launch": sweep_bytes, "sweep_ms": sweep_ms,
                      "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
                      "step_bytes_alg": step_bytes,
@@ -453,6 +551,7 @@ def run_ours(args):
         "kernel_ms": {"init": init_ms, "sweep": sweep_ms},
         "verdict": {"flags": v_end.flags, "n_pairs": v_end.n_pairs},
         "batched": batched,
+        "served": served,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": 2 * args.steps,

@@ -68,6 +68,8 @@ typedef struct mm_graph mm_graph;
 typedef struct mm_options {
     uint32_t status_bits;    /* 8: one state byte per vertex, 4 packed in a word
                                 (the paper's one byte per vertex, Section IV-C);
+                                2: the same three states in 2 bits, 16 vertices
+                                a word (a quarter of the paper's footprint);
                                 32: one word per vertex that is also the mate
                                 entry (ACC = MM_UNMATCHED, RSVD = 0xFFFFFFFE,
                                 matched = partner id).  0 = 8. */
@@ -88,7 +90,9 @@ typedef struct mm_options {
                                 captured once per handle and option set */
     uint32_t l2_persist;     /* 1: L2 access-policy window (persisting) over the
                                 state array for the sweep; 0 = per-load hints only */
-    uint32_t reserved0;
+    uint32_t stats;          /* 1: count reads, attempts and JIT conflicts in the
+                                sweep (slower kernel instance); read back with
+                                mm_get_stats() */
     uint64_t spin_limit;     /* polls of one wait before the call fails with
                                 MM_ERR_TIMEOUT; 0 = 1 << 20 */
     uint64_t poison_vertex;  /* fault injection for tests: v + 1 leaves vertex v
@@ -106,6 +110,26 @@ typedef struct mm_timing {
     uint64_t units;          /* merge-path work units of the sweep */
     uint64_t reserved[3];
 } mm_timing;
+
+/*
+ * Sweep statistics of the last mm_skipper call made with options.stats = 1.
+ * A conflict is a failed CAS at Algorithm 1 line 11 or 14 (Section VI-E,
+ * Table II); a CAS on a packed word that lost only to a neighbouring vertex's
+ * field is retried and not counted.  hist[] counts entries by their number of
+ * conflicts in Table II's bins: 1, 2, 3-4, 5-8, 9-16, 17-32, 33-64, 65-128,
+ * 129-256, >256.
+ */
+typedef struct mm_stats {
+    uint64_t entries_read;      /* neighbour ids the sweep loaded (matched rows are not read) */
+    uint64_t windows;           /* 32-row windows loaded */
+    uint64_t chunks;            /* chunks of up to 128 entries */
+    uint64_t attempts;          /* entries that reached line 11 */
+    uint64_t matches;           /* successful claims at line 14 */
+    uint64_t conflicts;         /* failed CAS at lines 11 and 14 */
+    uint64_t conflicted_entries;
+    uint64_t max_conflicts;     /* on one entry */
+    uint64_t hist[10];
+} mm_stats;
 
 /*
  * Verdict of mm_validate (the exact checker, Section II-B).  flags == 0 means
@@ -217,6 +241,10 @@ mm_status mm_validate(mm_graph *g, const uint32_t *d_mate, const uint32_t *d_pai
  * (MM_OK, MM_ERR_TIMEOUT or MM_ERR_BAD_GRAPH).  Used after nosync calls. */
 mm_status mm_sync(mm_graph *g, void *cuda_stream);
 
+/* Statistics of the last mm_skipper call made with o->stats = 1 (waits for it).
+ * MM_ERR_ARG when no such call was made. */
+mm_status mm_get_stats(mm_graph *g, mm_stats *out, void *cuda_stream);
+
 /* Per-kernel times of the last call made with o->timing = 1 (waits for its
  * events).  MM_ERR_ARG when no timed call was made since the last
  * mm_timing_history. */
@@ -229,8 +257,8 @@ mm_status mm_get_timing(mm_graph *g, mm_timing *out);
 mm_status mm_timing_history(mm_graph *g, mm_timing *out, uint32_t max, uint32_t *count);
 
 /*
- * Autotuner for mm_skipper_batched: times the candidate (grain, status_bits,
- * block_threads) settings on this batch with CUDA events, keeps the fastest
+ * Autotuner for mm_skipper_batched: times the candidate (grain, status_bits
+ * in {2, 8, 32}, block_threads) settings on this batch with CUDA events, keeps the fastest
  * whose result passes the device checker, and writes it into *o (other fields
  * of *o are kept).  d_mate_scratch: uint32_t[n].  Synchronous.
  */

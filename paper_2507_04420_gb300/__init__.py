@@ -18,7 +18,7 @@ from typing import Optional
 import torch
 
 from . import _native
-from ._native import GraphDesc, Options, Timing, Verdict
+from ._native import GraphDesc, Options, Stats, Timing, Verdict
 
 __all__ = ["Graph", "HostSession", "Multi", "SkipperError", "match", "validate", "Options", "Verdict", "Timing",
            "UNMATCHED", "lib", "options"]
@@ -154,6 +154,12 @@ class Graph:
                                _stream_ptr(stream)), "mm_validate")
         return v
 
+    def stats(self, stream=None) -> dict:
+        """Sweep statistics of the last skipper(stats=1) call (reads, JIT conflicts)."""
+        st = Stats()
+        _check(lib.mm_get_stats(self._h, ctypes.byref(st), _stream_ptr(stream)), "mm_get_stats")
+        return st.as_dict()
+
     @staticmethod
     def _tdict(t) -> dict:
         return {"init_ms": t.init_ms, "sweep_ms": t.sweep_ms, "compact_ms": t.compact_ms,
@@ -270,9 +276,10 @@ class HostSession:
         self.d_nb = torch.empty(max(nnz_max, 4), dtype=torch.int32, device=dev)
         self.d_mate = torch.empty(max(n_max, 1), dtype=torch.int32, device=dev)
         self._graphs = {}
+        self.last_verdict = None
 
     def run(self, offsets: torch.Tensor, nbrs: torch.Tensor, mate_out: Optional[torch.Tensor] = None,
-            stream=None, **kw) -> torch.Tensor:
+            stream=None, check: bool = False, **kw) -> torch.Tensor:
         n, nnz = offsets.numel() - 1, nbrs.numel()
         if n > self.n_max or nnz > self.nnz_max:
             raise ValueError("graph larger than the session's buffers")
@@ -285,6 +292,7 @@ class HostSession:
             self.close()
             g = self._graphs[key] = Graph(off_d, nb_d, check=False, stream=stream)
         g.skipper(mate=mate_d, stream=stream, **kw)
+        self.last_verdict = g.validate(mate_d, stream=stream) if check else None
         if mate_out is None:
             mate_out = torch.empty(n, dtype=torch.int32, pin_memory=True)
         mate_out.copy_(mate_d, non_blocking=True)

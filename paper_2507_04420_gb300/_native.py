@@ -20,7 +20,7 @@ INCLUDE = os.path.join(_ROOT, "include")
 LIB_DIR = os.path.join(_PKG, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libskipper.so")
 SOURCES = ["sweep.cu", "check.cu", "api.cu", "noalloc.cu", "multi.cu"]
-HEADERS = ["state.cuh", "internal.h", "walk.cuh"]
+HEADERS = ["state.cuh", "internal.h", "walk.cuh", "checkwalk.cuh"]
 
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
@@ -83,7 +83,7 @@ class Options(ctypes.Structure):
         ("timing", ctypes.c_uint32),
         ("use_graph", ctypes.c_uint32),
         ("l2_persist", ctypes.c_uint32),
-        ("reserved0", ctypes.c_uint32),
+        ("stats", ctypes.c_uint32),
         ("spin_limit", ctypes.c_uint64),
         ("poison_vertex", ctypes.c_uint64),
         ("reserved", ctypes.c_uint64 * 4),
@@ -109,6 +109,25 @@ class GraphDesc(ctypes.Structure):
         ("nbrs", ctypes.c_void_p),
         ("mate", ctypes.c_void_p),
     ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("entries_read", ctypes.c_uint64),
+        ("windows", ctypes.c_uint64),
+        ("chunks", ctypes.c_uint64),
+        ("attempts", ctypes.c_uint64),
+        ("matches", ctypes.c_uint64),
+        ("conflicts", ctypes.c_uint64),
+        ("conflicted_entries", ctypes.c_uint64),
+        ("max_conflicts", ctypes.c_uint64),
+        ("hist", ctypes.c_uint64 * 10),
+    ]
+
+    def as_dict(self):
+        d = {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "hist"}
+        d["hist"] = [int(x) for x in self.hist]
+        return d
 
 
 class Verdict(ctypes.Structure):
@@ -143,6 +162,7 @@ SYMBOLS = [
     ("mm_skipper_batched", _I, [_P, _U64, _P, _P, ctypes.POINTER(Options), _P, _P, _P]),
     ("mm_validate", _I, [_P, _P, _P, _U64, ctypes.POINTER(Verdict), _P]),
     ("mm_sync", _I, [_P, _P]),
+    ("mm_get_stats", _I, [_P, ctypes.POINTER(Stats), _P]),
     ("mm_get_timing", _I, [_P, ctypes.POINTER(Timing)]),
     ("mm_timing_history", _I, [_P, ctypes.POINTER(Timing), _U32, ctypes.POINTER(_U32)]),
     ("mm_autotune_batched", _I, [_P, _U64, _P, _P, _P, ctypes.POINTER(Options), _P]),

@@ -72,6 +72,10 @@ struct mm_graph {
   unsigned long long* ctrl = nullptr;  // [0] work counter, [1] err word, [2] csr-check count,
                                        // [8..16] checker counters
   uint32_t* seen_bits = nullptr;
+  unsigned long long* stats = nullptr;  // sweep statistics, allocated on first stats call
+  bool stats_valid = false;
+  unsigned char* found = nullptr;      // checker scratch, allocated on first mm_validate
+  int64_t* check_part = nullptr;
   uint64_t* tile_counts = nullptr;
   uint64_t tile_cap = 0;
   uint32_t* h_err = nullptr;           // pinned
@@ -96,12 +100,13 @@ unsigned long long* csr_bad_ptr(mm_graph* g) { return g->ctrl + 2; }
 unsigned long long* counters_ptr(mm_graph* g) { return g->ctrl + 8; }
 
 struct Resolved {
+  int bits;   // state layout: 2, 8 (packed fields) or 32 (word = mate)
   bool word;
   bool serial;
   uint32_t grain;
   int block;
   int blocks_per_sm;
-  bool nosync, timing, use_graph, l2_persist;
+  bool nosync, timing, use_graph, l2_persist, stats;
   uint64_t spin_limit, poison;
 };
 
@@ -110,7 +115,9 @@ mm_status resolve(const mm_graph* g, const mm_options* o, Resolved* r) {
   mm_default_options(&d);
   if (!o) o = &d;
   const uint32_t bits = o->status_bits ? o->status_bits : 8u;
-  if (bits != 8 && bits != 32) return fail(MM_ERR_ARG, "status_bits must be 8 or 32 (got %u)", bits);
+  if (bits != 2 && bits != 8 && bits != 32)
+    return fail(MM_ERR_ARG, "status_bits must be 2, 8 or 32 (got %u)", bits);
+  r->bits = (int)bits;
   r->word = bits == 32;
   r->serial = o->serial != 0;
   r->grain = o->grain ? o->grain : kDefaultGrain;
@@ -124,6 +131,7 @@ mm_status resolve(const mm_graph* g, const mm_options* o, Resolved* r) {
   r->timing = o->timing != 0;
   r->use_graph = o->use_graph != 0;
   r->l2_persist = o->l2_persist != 0;
+  r->stats = o->stats != 0;
   r->spin_limit = o->spin_limit ? o->spin_limit : kDefaultSpin;
   r->poison = o->poison_vertex;
   if (r->poison > g->n) return fail(MM_ERR_ARG, "poison_vertex out of range");
@@ -142,7 +150,7 @@ mm_status ensure_part(mm_graph* g, uint64_t units) {
 }
 
 int sweep_grid(const mm_graph* g, const Resolved& r) {
-  const int per_sm = r.blocks_per_sm > 0 ? r.blocks_per_sm : sweep_blocks_per_sm(r.word, r.block);
+  const int per_sm = r.blocks_per_sm > 0 ? r.blocks_per_sm : sweep_blocks_per_sm(r.bits, r.block);
   return g->num_sms * per_sm;
 }
 
@@ -350,24 +358,30 @@ mm_status mm_skipper(mm_graph* g, const mm_options* o, uint32_t* d_mate, uint32_
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const uint64_t units = (g->n + g->nnz + r.grain - 1) / r.grain;
   if ((st = ensure_part(g, units)) != MM_OK) return st;
-  const SweepParams P = make_params(g, r, d_mate);
+  SweepParams P = make_params(g, r, d_mate);
+  g->stats_valid = false;
+  if (r.stats && !r.serial) {
+    if (!g->stats) CUDA_TRY(cudaMalloc(&g->stats, kStCount * sizeof(unsigned long long)));
+    P.stats = g->stats;
+    g->stats_valid = true;
+  }
 
-  CheckScratch cs{counters_ptr(g), g->seen_bits, g->tile_counts, g->tile_cap};
+  CheckScratch cs{counters_ptr(g), g->seen_bits, g->tile_counts, g->tile_cap, nullptr, nullptr};
   cudaEvent_t* ev = nullptr;
   if (r.timing) {
     if ((st = ensure_hist(g)) != MM_OK) return st;
     ev = next_hist(g, units, d_pairs || d_count);
     CUDA_TRY(cudaEventRecord(ev[0], s));
   }
-  CUDA_TRY(launch_prepare(P, r.word, prepare_grid(g), s, nullptr, 0));
+  CUDA_TRY(launch_prepare(P, r.bits, prepare_grid(g), s, nullptr, 0));
   if (ev) CUDA_TRY(cudaEventRecord(ev[1], s));
   L2Window win;
   if (!r.serial) {
-    if ((st = win.open(g, r, s, P.state, r.word ? g->n * 4 : (g->n + 3) / 4 * 4)) != MM_OK) return st;
-    CUDA_TRY(launch_sweep(P, r.word, sweep_grid(g, r), r.block, s));
+    if ((st = win.open(g, r, s, P.state, r.word ? g->n * 4 : packed_words(g->n, r.bits) * 4)) != MM_OK) return st;
+    CUDA_TRY(launch_sweep(P, r.bits, sweep_grid(g, r), r.block, s));
     if ((st = win.close()) != MM_OK) return st;
   } else {
-    CUDA_TRY(launch_serial(P, r.word, s));
+    CUDA_TRY(launch_serial(P, r.bits, s));
   }
   if (ev) CUDA_TRY(cudaEventRecord(ev[2], s));
   if (d_pairs || d_count) {
@@ -385,6 +399,16 @@ mm_status mm_sync(mm_graph* g, void* cuda_stream) {
   mm_status st = check_handle(g);
   if (st != MM_OK) return st;
   return read_err(g, static_cast<cudaStream_t>(cuda_stream));
+}
+
+mm_status mm_get_stats(mm_graph* g, mm_stats* out, void* cuda_stream) {
+  if (!g || !out) return fail(MM_ERR_ARG, "null argument");
+  if (!g->stats_valid) return fail(MM_ERR_ARG, "no mm_skipper call with stats = 1");
+  static_assert(sizeof(mm_stats) == kStCount * sizeof(unsigned long long), "mm_stats layout");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  CUDA_TRY(cudaMemcpyAsync(out, g->stats, sizeof(mm_stats), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return MM_OK;
 }
 
 mm_status mm_get_timing(mm_graph* g, mm_timing* out) {
@@ -419,7 +443,7 @@ mm_status build_batch_graph(mm_graph* g, const Resolved& r, uint64_t num_graphs,
   b = BatchGraph{};
   CUDA_TRY(cudaGraphCreate(&b.graph, 0));
   const void *k_prepare = nullptr, *k_sweep = nullptr, *k_pairs = nullptr;
-  get_batched_kernels(r.word, r.serial, &k_prepare, &k_sweep, &k_pairs);
+  get_batched_kernels(r.bits, r.serial, &k_prepare, &k_sweep, &k_pairs);
 
   SweepParams p = P;
   uint64_t* gp = graph_pairs;
@@ -464,7 +488,7 @@ mm_status build_batch_graph(mm_graph* g, const Resolved& r, uint64_t num_graphs,
                                     sizeof(uint32_t), cudaMemcpyDeviceToHost));
   CUDA_TRY(cudaGraphInstantiate(&b.exec, b.graph, 0));
   b.valid = true;
-  b.status_bits = r.word ? 32 : 8;
+  b.status_bits = (uint32_t)r.bits;
   b.serial = r.serial;
   b.grain = r.grain;
   b.block = (uint32_t)r.block;
@@ -478,7 +502,7 @@ mm_status update_batch_graph(mm_graph* g, const Resolved& r, uint64_t num_graphs
                              const SweepParams& P, uint64_t* graph_pairs) {
   BatchGraph& b = g->bg;
   const void *k_prepare = nullptr, *k_sweep = nullptr, *k_pairs = nullptr;
-  get_batched_kernels(r.word, r.serial, &k_prepare, &k_sweep, &k_pairs);
+  get_batched_kernels(r.bits, r.serial, &k_prepare, &k_sweep, &k_pairs);
   SweepParams p = P;
   uint64_t* gp = graph_pairs;
   uint64_t ng = num_graphs;
@@ -536,7 +560,7 @@ mm_status mm_skipper_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d_
   if (r.use_graph) {
     BatchGraph& b = g->bg;
     const bool with_pairs = d_graph_pairs != nullptr;
-    const bool same = b.valid && b.status_bits == (r.word ? 32u : 8u) && b.serial == (uint32_t)r.serial &&
+    const bool same = b.valid && b.status_bits == (uint32_t)r.bits && b.serial == (uint32_t)r.serial &&
                       b.grain == r.grain && b.block == (uint32_t)r.block &&
                       b.blocks_per_sm == (uint32_t)r.blocks_per_sm && b.with_pairs == with_pairs &&
                       b.num_graphs == num_graphs && units <= g->part_units_cap;
@@ -556,12 +580,12 @@ mm_status mm_skipper_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d_
     ev = next_hist(g, units, d_graph_pairs != nullptr);
     CUDA_TRY(cudaEventRecord(ev[0], s));
   }
-  CUDA_TRY(launch_prepare(P, r.word, prepare_grid(g), s, d_graph_pairs, d_graph_pairs ? num_graphs : 0));
+  CUDA_TRY(launch_prepare(P, r.bits, prepare_grid(g), s, d_graph_pairs, d_graph_pairs ? num_graphs : 0));
   if (ev) CUDA_TRY(cudaEventRecord(ev[1], s));
   if (r.serial)
-    CUDA_TRY(launch_serial_batched(P, r.word, s));
+    CUDA_TRY(launch_serial_batched(P, r.bits, s));
   else
-    CUDA_TRY(launch_sweep(P, r.word, sweep_grid(g, r), r.block, s));
+    CUDA_TRY(launch_sweep(P, r.bits, sweep_grid(g, r), r.block, s));
   if (ev) CUDA_TRY(cudaEventRecord(ev[2], s));
   if (d_graph_pairs)
     CUDA_TRY(launch_graph_pairs(d_mate, d_vbase, num_graphs, g->n, d_graph_pairs, prepare_grid(g), s));
@@ -581,8 +605,11 @@ mm_status mm_validate(mm_graph* g, const uint32_t* d_mate, const uint32_t* d_pai
   if (d_pairs && count && !g->seen_bits)
     CUDA_TRY(cudaMalloc(&g->seen_bits, ((g->n + 31) / 32 + 1) * sizeof(uint32_t)));
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  CheckScratch cs{counters_ptr(g), g->seen_bits, g->tile_counts, g->tile_cap};
-  CUDA_TRY(launch_validate(g->n, g->offsets, g->nbrs, d_mate, d_pairs, d_pairs ? count : 0, cs,
+  if (!g->found) CUDA_TRY(cudaMalloc(&g->found, g->n + 16));
+  if (!g->check_part)
+    CUDA_TRY(cudaMalloc(&g->check_part, ((g->n + g->nnz) / kCheckGrain + 2) * 2 * sizeof(int64_t)));
+  CheckScratch cs{counters_ptr(g), g->seen_bits, g->tile_counts, g->tile_cap, g->found, g->check_part};
+  CUDA_TRY(launch_validate(g->n, g->nnz, g->offsets, g->nbrs, d_mate, d_pairs, d_pairs ? count : 0, cs,
                            prepare_grid(g), s));
   CUDA_TRY(cudaMemcpyAsync(g->h_counters, counters_ptr(g), 9 * sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, s));
@@ -615,7 +642,7 @@ mm_status mm_autotune_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d
   if (st != MM_OK) return st;
   if (!o || !d_mate_scratch) return fail(MM_ERR_ARG, "null options or scratch");
   static const uint32_t grains[] = {1024, 2048, 4096, 8192};
-  static const uint32_t bits[] = {8, 32};
+  static const uint32_t bits[] = {2, 8, 32};
   static const uint32_t blocks[] = {256, 512};
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   float best = 1e30f;
@@ -667,6 +694,9 @@ mm_status mm_destroy(mm_graph* g) {
   if (g->part) cudaFree(g->part);
   if (g->ctrl) cudaFree(g->ctrl);
   if (g->seen_bits) cudaFree(g->seen_bits);
+  if (g->found) cudaFree(g->found);
+  if (g->stats) cudaFree(g->stats);
+  if (g->check_part) cudaFree(g->check_part);
   if (g->tile_counts) cudaFree(g->tile_counts);
   if (g->h_err) cudaFreeHost(g->h_err);
   if (g->h_counters) cudaFreeHost(g->h_counters);

@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "checkwalk.cuh"
+#include "walk.cuh"
 
 namespace skp {
 
@@ -49,18 +51,55 @@ __device__ __forceinline__ void warp_add(unsigned long long* c, uint32_t v) {
   if ((threadIdx.x & 31) == 0 && s) atomicAdd(c, (unsigned long long)s);
 }
 
-// vertex pass: range / symmetry / existence of each named partner, and the
-// coverage of every entry of each unmatched row
-__global__ void validate_vertex_kernel(uint64_t n, const int64_t* __restrict__ offsets,
-                                       const uint32_t* __restrict__ nbrs,
-                                       const uint32_t* __restrict__ mate,
+// Merge-path split of rows + entries into units of `grain` items (the same
+// split the sweep uses), for the checker's edge pass.
+__global__ void check_partition_kernel(uint64_t n, uint64_t nnz, const int64_t* __restrict__ offsets,
+                                       uint64_t grain, uint64_t units, int64_t* __restrict__ part) {
+  const int64_t total = (int64_t)(n + nnz);
+  for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u <= units;
+       u += (uint64_t)gridDim.x * blockDim.x) {
+    int64_t d = (int64_t)(u * grain);
+    if (d > total) d = total;
+    const int64_t rows = merge_path_rows(offsets, (int64_t)n, (int64_t)nnz, d);
+    part[2 * u] = rows;
+    part[2 * u + 1] = d - rows;
+  }
+}
+
+// edge pass (checkwalk.cuh): uncovered entries, and found[x] for every x whose
+// partner appears in row x
+__global__ void validate_edges_kernel(uint64_t n, uint64_t nnz, const int64_t* __restrict__ offsets,
+                                      const uint32_t* __restrict__ nbrs,
+                                      const uint32_t* __restrict__ mate,
+                                      unsigned char* __restrict__ found,
+                                      const int64_t* __restrict__ part, uint64_t units,
+                                      unsigned long long* __restrict__ c) {
+  const unsigned lane = threadIdx.x & 31u;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long unc = 0, first = ~0ull;
+  for (uint64_t u = warp; u < units; u += nwarps) {
+    const int64_t e0 = part[2 * u + 1], e1 = part[2 * u + 3];
+    if (e0 < e1) check_unit(offsets, nbrs, n, nnz, mate, found, part[2 * u], e0, e1, lane, unc, first);
+  }
+  unc = warp_sum64(unc);
+  first = warp_min64(first);
+  if (lane == 0) {
+    if (unc) atomicAdd(c + C_UNCOVERED, unc);
+    if (first != ~0ull) atomicMin(c + C_FIRST_UNCOVERED, first);
+  }
+}
+
+// vertex pass: range / symmetry of each named partner, and its existence
+// from the edge pass's found marks
+__global__ void validate_vertex_kernel(uint64_t n, const uint32_t* __restrict__ mate,
+                                       const unsigned char* __restrict__ found,
                                        unsigned long long* __restrict__ c) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t v0 = (uint64_t)blockIdx.x * blockDim.x; v0 < n; v0 += stride) {
     const uint64_t v = v0 + threadIdx.x;
-    uint32_t matched = 0, pair = 0, range = 0, asym = 0, nonedge = 0, uncovered = 0;
+    uint32_t matched = 0, pair = 0, range = 0, asym = 0, nonedge = 0;
     bool bad = false;
-    unsigned long long first_unc = ~0ull;
     if (v < n) {
       const uint32_t m = mate[v];
       if (m != kNone) {
@@ -75,21 +114,9 @@ __global__ void validate_vertex_kernel(uint64_t n, const int64_t* __restrict__ o
           } else if (v < m) {
             pair = 1;
           }
-          // the edge may be stored in the row of either endpoint
-          bool found = false;
-          for (int64_t i = offsets[v]; i < offsets[v + 1] && !found; ++i) found = nbrs[i] == m;
-          for (int64_t i = offsets[m]; i < offsets[m + 1] && !found; ++i) found = nbrs[i] == (uint32_t)v;
-          if (!found) {
+          if (!found[v] && !found[m]) {  // the edge may be stored for either endpoint
             nonedge = 1;
             bad = true;
-          }
-        }
-      } else {
-        for (int64_t i = offsets[v]; i < offsets[v + 1]; ++i) {
-          const uint32_t y = nbrs[i];
-          if (y != (uint32_t)v && y < n && mate[y] == kNone) {
-            ++uncovered;
-            if ((unsigned long long)i < first_unc) first_unc = (unsigned long long)i;
           }
         }
       }
@@ -99,10 +126,8 @@ __global__ void validate_vertex_kernel(uint64_t n, const int64_t* __restrict__ o
     warp_add(c + C_RANGE, range);
     warp_add(c + C_ASYM, asym);
     warp_add(c + C_NONEDGE, nonedge);
-    warp_add(c + C_UNCOVERED, uncovered);
     const uint32_t first_bad = __reduce_min_sync(kFull, bad ? (uint32_t)v : kNone);
     if ((threadIdx.x & 31) == 0 && first_bad != kNone) atomicMin(c + C_FIRST_BAD, (unsigned long long)first_bad);
-    if (first_unc != ~0ull) atomicMin(c + C_FIRST_UNCOVERED, first_unc);
   }
 }
 
@@ -237,13 +262,19 @@ cudaError_t launch_csr_check(uint64_t n, uint64_t nnz, const int64_t* offsets,
   return cudaGetLastError();
 }
 
-cudaError_t launch_validate(uint64_t n, const int64_t* offsets, const uint32_t* nbrs,
+cudaError_t launch_validate(uint64_t n, uint64_t nnz, const int64_t* offsets, const uint32_t* nbrs,
                             const uint32_t* mate, const uint32_t* pairs, uint64_t count,
                             const CheckScratch& cs, int grid, cudaStream_t s) {
   zero_u64_kernel<<<1, 32, 0, s>>>(cs.counters, C_FIRST_BAD, 0ull);
   zero_u64_kernel<<<1, 32, 0, s>>>(cs.counters + C_FIRST_BAD, 2, ~0ull);
   if (pairs && count) zero_u32_kernel<<<grid, 256, 0, s>>>(cs.seen_bits, (n + 31) / 32);
-  if (n) validate_vertex_kernel<<<grid, 256, 0, s>>>(n, offsets, nbrs, mate, cs.counters);
+  if (n) {
+    zero_u32_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<uint32_t*>(cs.found), (n + 3) / 4);
+    const uint64_t units = (n + nnz + kCheckGrain - 1) / kCheckGrain;
+    check_partition_kernel<<<grid, 256, 0, s>>>(n, nnz, offsets, kCheckGrain, units, cs.part);
+    if (nnz) validate_edges_kernel<<<grid, 256, 0, s>>>(n, nnz, offsets, nbrs, mate, cs.found, cs.part, units, cs.counters);
+    validate_vertex_kernel<<<grid, 256, 0, s>>>(n, mate, cs.found, cs.counters);
+  }
   if (pairs && count) validate_pairs_kernel<<<grid, 256, 0, s>>>(n, mate, pairs, count, cs.seen_bits, cs.counters);
   return cudaGetLastError();
 }

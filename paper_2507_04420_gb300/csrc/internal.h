@@ -7,14 +7,14 @@
 
 namespace skp {
 
-// sweep.cu
-int sweep_blocks_per_sm(bool word, int block_threads);
-cudaError_t launch_prepare(const SweepParams& P, bool word, int grid, cudaStream_t s,
+// sweep.cu (bits: 2, 8 or 32 -- the state layout, see state.cuh)
+int sweep_blocks_per_sm(int bits, int block_threads);
+cudaError_t launch_prepare(const SweepParams& P, int bits, int grid, cudaStream_t s,
                            uint64_t* graph_pairs_zero, uint64_t num_graphs);
-cudaError_t launch_sweep(const SweepParams& P, bool word, int grid, int block, cudaStream_t s);
-cudaError_t launch_serial(const SweepParams& P, bool word, cudaStream_t s);
-cudaError_t launch_serial_batched(const SweepParams& P, bool word, cudaStream_t s);
-void get_batched_kernels(bool word, bool serial, const void** prepare, const void** sweep,
+cudaError_t launch_sweep(const SweepParams& P, int bits, int grid, int block, cudaStream_t s);
+cudaError_t launch_serial(const SweepParams& P, int bits, cudaStream_t s);
+cudaError_t launch_serial_batched(const SweepParams& P, int bits, cudaStream_t s);
+void get_batched_kernels(int bits, bool serial, const void** prepare, const void** sweep,
                          const void** pairs);
 cudaError_t launch_graph_pairs(const uint32_t* mate, const int64_t* vbase, uint64_t num_graphs,
                                uint64_t n, uint64_t* graph_pairs, int grid, cudaStream_t s);
@@ -28,11 +28,14 @@ struct CheckScratch {
   uint32_t* seen_bits;           // ceil(n/32) words
   uint64_t* block_counts;        // compaction: one count per tile of vertices
   uint64_t block_cap;
+  unsigned char* found;          // checker: n bytes (+3), partner edge seen in the row
+  int64_t* part;                 // checker: merge-path table, (n+nnz)/kCheckGrain + 1 pairs
 };
+constexpr uint64_t kCheckGrain = 4096;  // rows + entries per checker work unit
 cudaError_t launch_csr_check(uint64_t n, uint64_t nnz, const int64_t* offsets,
                              const uint32_t* nbrs, unsigned long long* bad, int grid,
                              cudaStream_t s);
-cudaError_t launch_validate(uint64_t n, const int64_t* offsets, const uint32_t* nbrs,
+cudaError_t launch_validate(uint64_t n, uint64_t nnz, const int64_t* offsets, const uint32_t* nbrs,
                             const uint32_t* mate, const uint32_t* pairs, uint64_t count,
                             const CheckScratch& cs, int grid, cudaStream_t s);
 constexpr uint64_t kCompactTile = 4096;  // vertices per compaction tile

@@ -20,6 +20,7 @@
 #include "internal.h"
 #include "skipper.h"
 #include "walk.cuh"
+#include "checkwalk.cuh"
 
 using namespace skp;
 
@@ -32,7 +33,7 @@ struct MultiParams {
   const uint64_t* ubase;      // [G+1] first unit of each graph
   const uint64_t* vbase;      // [G+1] first vertex of each graph (for the init pass)
   const uint64_t* sbase;      // [G+1] first packed state word of each graph
-  uint32_t* state_pool;       // ByteState words of all graphs
+  uint32_t* state_pool;       // packed state words of all graphs (2- or 8-bit layouts)
   int64_t* part;              // (row, entry) per unit
   uint32_t* gid;              // graph of each unit
   uint64_t units;
@@ -41,6 +42,7 @@ struct MultiParams {
   uint32_t* err;
   uint64_t spin_limit;
   unsigned long long* counters;  // checker: 9 per graph
+  unsigned char* found;          // checker: one byte per vertex of every graph
 };
 
 // last g with base[g] <= x, base[0] = 0, base ascending, g < G
@@ -147,8 +149,54 @@ __device__ __forceinline__ void group_add(unsigned long long* c, unsigned peers,
   if ((int)(threadIdx.x & 31) == __ffs(peers) - 1 && s) atomicAdd(c, (unsigned long long)s);
 }
 
-// the single-graph checker's vertex pass (check.cu) on every vertex of every
-// graph, with the counters of each graph kept apart
+__global__ void multi_partition_kernel(MultiParams M) {
+  const uint64_t G = M.num_graphs;
+  for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < M.units;
+       u += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t g = find_graph(M.ubase, G, u);
+    const mm_graph_desc d = M.desc[g];
+    const int64_t total = (int64_t)(d.n + d.nnz);
+    int64_t diag = (int64_t)((u - M.ubase[g]) * M.grain);
+    if (diag > total) diag = total;
+    const int64_t rows = merge_path_rows(d.offsets, (int64_t)d.n, (int64_t)d.nnz, diag);
+    M.part[2 * u] = rows;
+    M.part[2 * u + 1] = diag - rows;
+    M.gid[u] = (uint32_t)g;
+  }
+}
+
+__global__ void multi_clear_found_kernel(MultiParams M) {
+  const uint64_t V = M.vbase[M.num_graphs];
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    M.found[i] = 0;
+}
+
+// the checker's edge pass (checkwalk.cuh) over the units of every graph
+__global__ void multi_validate_edges_kernel(MultiParams M) {
+  const unsigned lane = threadIdx.x & 31u;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t u = warp; u < M.units; u += nwarps) {
+    const uint32_t g = M.gid[u];
+    const mm_graph_desc d = M.desc[g];
+    const int64_t e0 = M.part[2 * u + 1];
+    const int64_t e1 = (u + 1 < M.units && M.gid[u + 1] == g) ? M.part[2 * u + 3] : (int64_t)d.nnz;
+    if (e0 >= e1) continue;
+    unsigned long long unc = 0, first = ~0ull;
+    check_unit(d.offsets, d.nbrs, d.n, d.nnz, d.mate, M.found + M.vbase[g], M.part[2 * u], e0, e1,
+               lane, unc, first);
+    unc = warp_sum64(unc);
+    first = warp_min64(first);
+    if (lane == 0) {
+      unsigned long long* c = M.counters + (uint64_t)g * C_N;
+      if (unc) atomicAdd(c + C_UNCOVERED, unc);
+      if (first != ~0ull) atomicMin(c + C_FIRST_UNCOVERED, first);
+    }
+  }
+}
+
+// the checker's vertex pass on every vertex of every graph, counters kept per graph
 __global__ void multi_validate_kernel(MultiParams M) {
   const uint64_t G = M.num_graphs;
   const uint64_t V = M.vbase[G];
@@ -156,13 +204,14 @@ __global__ void multi_validate_kernel(MultiParams M) {
   for (uint64_t v0 = (uint64_t)blockIdx.x * blockDim.x; v0 < V; v0 += stride) {
     const uint64_t gv = v0 + threadIdx.x;
     uint64_t g = ~0ull;
-    uint32_t matched = 0, pair = 0, range = 0, asym = 0, nonedge = 0, uncovered = 0;
-    uint64_t first_bad = ~0ull, first_unc = ~0ull;
+    uint32_t matched = 0, pair = 0, range = 0, asym = 0, nonedge = 0;
+    uint64_t first_bad = ~0ull;
     if (gv < V) {
       g = find_graph(M.vbase, G, gv);
       const mm_graph_desc d = M.desc[g];
       const uint64_t v = gv - M.vbase[g];
       const uint64_t n = d.n;
+      const unsigned char* found = M.found + M.vbase[g];
       const uint32_t m = d.mate[v];
       if (m != kNone) {
         if (m >= n || m == v) {
@@ -176,20 +225,9 @@ __global__ void multi_validate_kernel(MultiParams M) {
           } else if (v < m) {
             pair = 1;
           }
-          bool found = false;
-          for (int64_t i = d.offsets[v]; i < d.offsets[v + 1] && !found; ++i) found = d.nbrs[i] == m;
-          for (int64_t i = d.offsets[m]; i < d.offsets[m + 1] && !found; ++i) found = d.nbrs[i] == (uint32_t)v;
-          if (!found) {
+          if (!found[v] && !found[m]) {
             nonedge = 1;
             first_bad = v;
-          }
-        }
-      } else {
-        for (int64_t i = d.offsets[v]; i < d.offsets[v + 1]; ++i) {
-          const uint32_t y = d.nbrs[i];
-          if (y != (uint32_t)v && y < n && d.mate[y] == kNone) {
-            ++uncovered;
-            if ((uint64_t)i < first_unc) first_unc = (uint64_t)i;
           }
         }
       }
@@ -203,9 +241,7 @@ __global__ void multi_validate_kernel(MultiParams M) {
       group_add(c + C_RANGE, peers, range);
       group_add(c + C_ASYM, peers, asym);
       group_add(c + C_NONEDGE, peers, nonedge);
-      group_add(c + C_UNCOVERED, peers, uncovered);
       if (first_bad != ~0ull) atomicMin(c + C_FIRST_BAD, (unsigned long long)first_bad);
-      if (first_unc != ~0ull) atomicMin(c + C_FIRST_UNCOVERED, (unsigned long long)first_unc);
     }
   }
 }
@@ -262,6 +298,8 @@ struct mm_multi {
   uint64_t pool_cap = 0;
   unsigned long long* counters = nullptr;
   uint64_t counters_cap = 0;
+  unsigned char* found = nullptr;
+  uint64_t found_cap = 0;
   unsigned long long* ctrl = nullptr;  // [0] work, [1] err
   uint32_t* h_err = nullptr;           // pinned
   unsigned long long* h_counters = nullptr;
@@ -278,7 +316,7 @@ struct Layout {
   uint64_t total_vertices = 0, total_words = 0;
 };
 
-mm_status stage_tables(mm_multi* m, uint64_t G, const mm_graph_desc* h, uint64_t grain,
+mm_status stage_tables(mm_multi* m, uint64_t G, const mm_graph_desc* h, uint64_t grain, int bits,
                        cudaStream_t s, Layout* L) {
   L->off_ubase = G * sizeof(mm_graph_desc);
   L->off_vbase = L->off_ubase + (G + 1) * 8;
@@ -305,7 +343,7 @@ mm_status stage_tables(mm_multi* m, uint64_t G, const mm_graph_desc* h, uint64_t
   for (uint64_t g = 0; g < G; ++g) {
     ub[g + 1] = ub[g] + (h[g].n + h[g].nnz + grain - 1) / grain;
     vb[g + 1] = vb[g] + h[g].n;
-    sb[g + 1] = sb[g] + (h[g].n + 3) / 4 + 1;
+    sb[g + 1] = sb[g] + (bits == 32 ? 0 : packed_words(h[g].n, bits) + 1);
   }
   L->units = ub[G];
   L->total_vertices = vb[G];
@@ -332,6 +370,7 @@ MultiParams params(mm_multi* m, uint64_t G, const Layout& L, uint64_t grain, uin
   M.err = reinterpret_cast<uint32_t*>(m->ctrl + 1);
   M.spin_limit = spin;
   M.counters = m->counters;
+  M.found = m->found;
   return M;
 }
 
@@ -382,7 +421,7 @@ mm_status mm_skipper_multi(mm_multi* m, uint64_t num_graphs, const mm_graph_desc
   mm_default_options(&d);
   if (!o) o = &d;
   const uint32_t bits = o->status_bits ? o->status_bits : 8u;
-  if (bits != 8 && bits != 32) return mfail(MM_ERR_ARG, "status_bits must be 8 or 32");
+  if (bits != 2 && bits != 8 && bits != 32) return mfail(MM_ERR_ARG, "status_bits must be 2, 8 or 32");
   const bool word = bits == 32;
   const uint64_t grain = o->grain ? o->grain : 2048;
   if (grain % 128 || grain > (1u << 24)) return mfail(MM_ERR_ARG, "bad grain");
@@ -393,7 +432,7 @@ mm_status mm_skipper_multi(mm_multi* m, uint64_t num_graphs, const mm_graph_desc
                                      "available in multi-graph calls");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   Layout L;
-  if ((st = stage_tables(m, num_graphs, h_descs, grain, s, &L)) != MM_OK) return st;
+  if ((st = stage_tables(m, num_graphs, h_descs, grain, (int)bits, s, &L)) != MM_OK) return st;
   MTRY(grow(&m->part, &m->part_cap, 2 * (L.units + 1)));
   MTRY(grow(&m->gid, &m->gid_cap, L.units + 1));
   if (!word) MTRY(grow(&m->pool, &m->pool_cap, L.total_words + 1));
@@ -405,17 +444,21 @@ mm_status mm_skipper_multi(mm_multi* m, uint64_t num_graphs, const mm_graph_desc
   MTRY(cudaGetLastError());
   if (o->serial) {
     const unsigned grid = (unsigned)((num_graphs + 127) / 128);
-    if (word) multi_serial_kernel<WordState, true><<<grid, 128, 0, s>>>(M);
+    if (bits == 32) multi_serial_kernel<WordState, true><<<grid, 128, 0, s>>>(M);
+    else if (bits == 2) multi_serial_kernel<TwoBitState, false><<<grid, 128, 0, s>>>(M);
     else multi_serial_kernel<ByteState, false><<<grid, 128, 0, s>>>(M);
   } else if (L.units) {
     int per_sm = (int)o->blocks_per_sm;
     if (per_sm <= 0) {
-      cudaError_t e = word ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, multi_sweep_kernel<WordState, true>, block, 0)
-                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, multi_sweep_kernel<ByteState, false>, block, 0);
+      cudaError_t e = bits == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, multi_sweep_kernel<WordState, true>, block, 0)
+                    : bits == 2  ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, multi_sweep_kernel<TwoBitState, false>, block, 0)
+                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, multi_sweep_kernel<ByteState, false>, block, 0);
       if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     }
-    if (word) multi_sweep_kernel<WordState, true><<<m->num_sms * per_sm, block, 0, s>>>(M);
-    else multi_sweep_kernel<ByteState, false><<<m->num_sms * per_sm, block, 0, s>>>(M);
+    const int grid = m->num_sms * per_sm;
+    if (bits == 32) multi_sweep_kernel<WordState, true><<<grid, block, 0, s>>>(M);
+    else if (bits == 2) multi_sweep_kernel<TwoBitState, false><<<grid, block, 0, s>>>(M);
+    else multi_sweep_kernel<ByteState, false><<<grid, block, 0, s>>>(M);
   }
   MTRY(cudaGetLastError());
   MTRY(cudaMemcpyAsync(m->h_err, M.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -441,8 +484,11 @@ mm_status mm_validate_multi(mm_multi* m, uint64_t num_graphs, const mm_graph_des
   if (st != MM_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   Layout L;
-  if ((st = stage_tables(m, num_graphs, h_descs, 1u << 24, s, &L)) != MM_OK) return st;
+  if ((st = stage_tables(m, num_graphs, h_descs, kCheckGrain, 32, s, &L)) != MM_OK) return st;
   MTRY(grow(&m->counters, &m->counters_cap, num_graphs * C_N));
+  MTRY(grow(&m->found, &m->found_cap, L.total_vertices + 16));
+  MTRY(grow(&m->part, &m->part_cap, 2 * (L.units + 1)));
+  MTRY(grow(&m->gid, &m->gid_cap, L.units + 1));
   if (m->h_counters_cap < num_graphs * C_N) {
     if (m->h_counters) cudaFreeHost(m->h_counters);
     m->h_counters = nullptr;
@@ -450,9 +496,17 @@ mm_status mm_validate_multi(mm_multi* m, uint64_t num_graphs, const mm_graph_des
     MTRY(cudaMallocHost(&m->h_counters, num_graphs * C_N * sizeof(unsigned long long)));
     m->h_counters_cap = num_graphs * C_N;
   }
-  const MultiParams M = params(m, num_graphs, L, 1u << 24, 1);
+  const MultiParams M = params(m, num_graphs, L, kCheckGrain, 1);
+  const int grid = m->num_sms * 8;
   multi_counters_init_kernel<<<m->num_sms * 4, 256, 0, s>>>(m->counters, num_graphs);
-  if (L.total_vertices) multi_validate_kernel<<<m->num_sms * 8, 256, 0, s>>>(M);
+  if (L.total_vertices) {
+    multi_clear_found_kernel<<<grid, 256, 0, s>>>(M);
+    if (L.units) {
+      multi_partition_kernel<<<grid, 256, 0, s>>>(M);
+      multi_validate_edges_kernel<<<grid, 256, 0, s>>>(M);
+    }
+    multi_validate_kernel<<<grid, 256, 0, s>>>(M);
+  }
   MTRY(cudaGetLastError());
   MTRY(cudaMemcpyAsync(m->h_counters, m->counters, num_graphs * C_N * sizeof(unsigned long long),
                        cudaMemcpyDeviceToHost, s));
@@ -488,6 +542,7 @@ mm_status mm_multi_destroy(mm_multi* m) {
   if (m->gid) cudaFree(m->gid);
   if (m->pool) cudaFree(m->pool);
   if (m->counters) cudaFree(m->counters);
+  if (m->found) cudaFree(m->found);
   if (m->ctrl) cudaFree(m->ctrl);
   if (m->h_err) cudaFreeHost(m->h_err);
   if (m->h_counters) cudaFreeHost(m->h_counters);

@@ -113,13 +113,13 @@ extern "C" mm_status mm_skipper_static(uint64_t n, uint64_t nnz, const int64_t* 
   P.poison = o->poison_vertex;
 
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  if (launch_prepare(P, false, sms * 8, s, nullptr, 0) != cudaSuccess) return MM_ERR_CUDA;
+  if (launch_prepare(P, 8, sms * 8, s, nullptr, 0) != cudaSuccess) return MM_ERR_CUDA;
   cudaError_t e;
   if (o->serial) {
-    e = launch_serial(P, false, s);
+    e = launch_serial(P, 8, s);
   } else {
-    const int per_sm = o->blocks_per_sm ? (int)o->blocks_per_sm : sweep_blocks_per_sm(false, block);
-    e = launch_sweep(P, false, sms * per_sm, block, s);
+    const int per_sm = o->blocks_per_sm ? (int)o->blocks_per_sm : sweep_blocks_per_sm(8, block);
+    e = launch_sweep(P, 8, sms * per_sm, block, s);
   }
   if (e != cudaSuccess) return MM_ERR_CUDA;
   uint32_t err = 0;  // the call's device status, read back into host stack memory

@@ -2,15 +2,17 @@
 // Algorithm 1) on GB300 global memory.
 //
 // Two layouts of the state array:
-//   ByteState: one byte per vertex (ACC = 0, RSVD = 1, MCHD = 2 as in
-//     Algorithm 1), four vertices packed in a 32-bit word.  Every access is a
-//     32-bit access to the whole word (relaxed loads, 32-bit CAS, 32-bit
-//     XOR), so all accesses to a location have the same size and are
-//     morally strong in the PTX memory model.  A byte CAS is a word CAS that
-//     is retried when only a neighbouring byte changed.  The holder-only
+//   PackedState<8> (ByteState): one byte per vertex (ACC = 0, RSVD = 1,
+//     MCHD = 2 as in Algorithm 1), four vertices packed in a 32-bit word;
+//     PackedState<2> (TwoBitState): the same three values in 2 bits, sixteen
+//     vertices a word, so the state array is a quarter of the paper's size.
+//     Every access is a 32-bit access to the whole word (relaxed loads, 32-bit
+//     CAS, 32-bit XOR), so all accesses to a location have the same size and
+//     are morally strong in the PTX memory model.  A field CAS is a word CAS
+//     that is retried when only a neighbouring field changed.  The holder-only
 //     transitions RSVD->MCHD and RSVD->ACC (Algorithm 1 lines 15 and 18, plain
 //     stores in the paper) become one atomic XOR on the word, which cannot
-//     disturb the neighbouring bytes.
+//     disturb the neighbouring fields.
 //   WordState: one 32-bit word per vertex that doubles as the mate entry:
 //     ACC = 0xFFFFFFFF (= unmatched), RSVD = 0xFFFFFFFE, MCHD = the partner id.
 //     Claiming v writes u into v's word directly; the holder then stores v into
@@ -35,7 +37,7 @@ struct SweepParams {
   uint64_t nnz;
   const int64_t* offsets;
   const uint32_t* nbrs;
-  uint32_t* state;      // ByteState: ceil(n/4) packed words; WordState: == mate
+  uint32_t* state;      // PackedState: packed words; WordState: == mate
   uint32_t* mate;
   int64_t* part;        // merge-path unit starts: (row, entry) for units+1 diagonals
   uint64_t units;
@@ -47,7 +49,35 @@ struct SweepParams {
   // batched serial mode
   const int64_t* vbase;
   uint64_t num_graphs;
+  // statistics (kStats kernels only): see StatSlot
+  unsigned long long* stats;
 };
+
+// Sweep statistics, kept only by the kStats kernel instances.  A conflict is a
+// failed CAS at Algorithm 1 line 11 or 14 (Section VI-E, Table II); a field CAS
+// that lost only to a neighbouring field is retried and not counted.
+enum StatSlot : int {
+  kStEntries = 0,   // neighbour ids read by the sweep
+  kStWindows,       // 32-row windows loaded
+  kStChunks,        // chunks of up to 128 entries read
+  kStAttempts,      // entries that reached Algorithm 1 line 11
+  kStMatches,       // successful claims (line 14)
+  kStConflicts,     // failed CAS at lines 11 and 14
+  kStConflicted,    // entries with at least one conflict
+  kStMaxConflicts,  // most conflicts on one entry
+  kStHist,          // 10 bins: 1, 2, 3-4, 5-8, 9-16, 17-32, 33-64, 65-128, 129-256, >256
+  kStCount = kStHist + 10
+};
+
+__device__ __forceinline__ void stat_conflicts(unsigned long long* st, uint32_t c) {
+  if (c == 0) return;
+  atomicAdd(st + kStConflicts, (unsigned long long)c);
+  atomicAdd(st + kStConflicted, 1ull);
+  atomicMax(st + kStMaxConflicts, (unsigned long long)c);
+  int bin = 0;
+  while (bin < 9 && c > (1u << bin)) ++bin;  // 1, 2, 3-4, 5-8, ... , >256
+  atomicAdd(st + kStHist + bin, 1ull);
+}
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
   uint32_t v;
@@ -116,27 +146,31 @@ struct Waiter {
 // such a word.  try_reserve / try_claim start from a word the caller has
 // already observed and, when they fail, leave in it the word the CAS met, so
 // a failed attempt costs no extra load.
-struct ByteState {
+template <int kBits>
+struct PackedState {
+  static constexpr uint32_t kPerWord = 32u / kBits;
+  static constexpr uint32_t kMask = (1u << kBits) - 1u;
   uint32_t* words;
   uint32_t* mate;
-  __device__ explicit ByteState(const SweepParams& P) : words(P.state), mate(P.mate) {}
-  __device__ static __forceinline__ uint32_t shift(uint32_t v) { return (v & 3u) << 3; }
-  __device__ __forceinline__ uint32_t raw(uint32_t v) const { return ld_relaxed(words + (v >> 2)); }
-  __device__ __forceinline__ uint32_t peek(uint32_t v) const { return ld_relaxed_nf(words + (v >> 2)); }
+  __device__ explicit PackedState(const SweepParams& P) : words(P.state), mate(P.mate) {}
+  __device__ static __forceinline__ uint32_t word(uint32_t v) { return v / kPerWord; }
+  __device__ static __forceinline__ uint32_t shift(uint32_t v) { return (v % kPerWord) * kBits; }
+  __device__ __forceinline__ uint32_t raw(uint32_t v) const { return ld_relaxed(words + word(v)); }
+  __device__ __forceinline__ uint32_t peek(uint32_t v) const { return ld_relaxed_nf(words + word(v)); }
   __device__ static __forceinline__ bool matched(uint32_t raw, uint32_t v) {
-    return ((raw >> shift(v)) & 0xFFu) == kMchd;
+    return ((raw >> shift(v)) & kMask) == kMchd;
   }
-  // Byte CAS from `expect` to `desired` starting at the observed word `cur`; a
-  // failure caused only by a neighbouring byte is retried (it is not a
-  // conflict on v).  On failure `cur` holds the word whose byte for v is not
+  // CAS of v's field from `expect` to `desired` starting at the observed word
+  // `cur`; a failure caused only by a neighbouring field is retried (it is not
+  // a conflict on v).  On failure `cur` holds the word whose field for v is not
   // `expect`.
   __device__ __forceinline__ bool cas(uint32_t v, uint32_t expect, uint32_t desired, uint32_t& cur,
                                       const SweepParams& P) const {
-    uint32_t* w = words + (v >> 2);
+    uint32_t* w = words + word(v);
     const uint32_t sh = shift(v);
     for (uint64_t tries = 0;; ++tries) {
-      if (((cur >> sh) & 0xFFu) != expect) return false;
-      const uint32_t next = (cur & ~(0xFFu << sh)) | (desired << sh);
+      if (((cur >> sh) & kMask) != expect) return false;
+      const uint32_t next = (cur & ~(kMask << sh)) | (desired << sh);
       const uint32_t old = atomicCAS(w, cur, next);
       if (old == cur) {
         cur = next;
@@ -160,13 +194,23 @@ struct ByteState {
   __device__ __forceinline__ void commit(uint32_t u, uint32_t v) const {
     mate[u] = v;
     mate[v] = u;
-    atomicXor(words + (u >> 2), (kRsvd ^ kMchd) << shift(u));
+    atomicXor(words + word(u), (kRsvd ^ kMchd) << shift(u));
   }
   // holder only: RSVD -> ACC
   __device__ __forceinline__ void release(uint32_t u) const {
-    atomicXor(words + (u >> 2), (kRsvd ^ kAcc) << shift(u));
+    atomicXor(words + word(u), (kRsvd ^ kAcc) << shift(u));
   }
 };
+
+// one state byte per vertex (the paper's layout) and a 2-bit field per vertex
+using ByteState = PackedState<8>;
+using TwoBitState = PackedState<2>;
+
+// words of the packed state array for n vertices at kBits per vertex
+__host__ __device__ __forceinline__ uint64_t packed_words(uint64_t n, int bits) {
+  const uint64_t per = 32u / (uint64_t)bits;
+  return (n + per - 1) / per;
+}
 
 struct WordState {
   uint32_t* words;
@@ -191,7 +235,7 @@ struct WordState {
 // already observed for x and y (they stand for the first line-10 read).
 // Returns true when the row vertex x is MCHD at the end (by this attempt or by
 // another thread), which lets the caller leave the rest of row x.
-template <class S>
+template <class S, bool kStats = false>
 __device__ __forceinline__ bool resolve_edge(const S& s, uint32_t x, uint32_t y, uint32_t rx,
                                              uint32_t ry, const SweepParams& P) {
   if (x == y) return S::matched(rx, x);      // lines 6-7: loops are skipped
@@ -199,31 +243,52 @@ __device__ __forceinline__ bool resolve_edge(const S& s, uint32_t x, uint32_t y,
   const uint32_t u = x_low ? x : y, v = x_low ? y : x;
   uint32_t ru = x_low ? rx : ry, rv = x_low ? ry : rx;
   Waiter wt;
+  uint32_t cnf = 0;                          // conflicts on this entry (kStats only)
+  bool result = false;
   for (;;) {
     // line 10
-    if (S::matched(ru, u) || S::matched(rv, v)) return S::matched(x_low ? ru : rv, x);
+    if (S::matched(ru, u) || S::matched(rv, v)) {
+      result = S::matched(x_low ? ru : rv, x);
+      break;
+    }
+    if (kStats && cnf == 0 && wt.polls == 0) atomicAdd(P.stats + kStAttempts, 1ull);
     if (!s.try_reserve(u, ru, P)) {          // lines 11-12: wait, then re-test line 10
-      if (S::matched(ru, u)) return x_low;
-      if (!wt.wait(P)) return false;
+      if (kStats) ++cnf;
+      if (S::matched(ru, u)) {
+        result = x_low;
+        break;
+      }
+      if (!wt.wait(P)) break;
       ru = s.raw(u);
       rv = s.raw(v);
       continue;
     }
+    bool won = false, gave_up = false;
     for (;;) {                               // lines 13-16, holding u
       if (s.try_claim(v, u, rv, P)) {
         s.commit(u, v);                      // lines 15-16
-        return true;
+        won = true;
+        break;
       }
+      if (kStats) ++cnf;
       if (S::matched(rv, v)) break;          // v went to another edge
       if (!wt.wait(P)) {
-        s.release(u);
-        return false;
+        gave_up = true;
+        break;
       }
       rv = s.raw(v);
     }
+    if (won) {
+      if (kStats) atomicAdd(P.stats + kStMatches, 1ull);
+      result = true;
+      break;
+    }
     s.release(u);                            // lines 17-18
-    return !x_low;
+    result = gave_up ? false : !x_low;
+    break;
   }
+  if (kStats) stat_conflicts(P.stats, cnf);
+  return result;
 }
 
 }  // namespace skp

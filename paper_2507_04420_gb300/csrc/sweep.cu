@@ -24,19 +24,20 @@ namespace skp {
 
 namespace {
 
-template <bool kWord>
+template <int kBits>
 __global__ void prepare_kernel(SweepParams P, uint64_t* graph_pairs, uint64_t num_graphs) {
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t n = P.n;
-  if (kWord) {
+  if (kBits == 32) {
     for (uint64_t v = tid; v < n; v += nthreads)
       P.state[v] = (P.poison && v == P.poison - 1) ? kWRsvd : kWAcc;
   } else {
-    const uint64_t nwords = (n + 3) >> 2;
+    constexpr uint64_t per = 32 / kBits;
+    const uint64_t nwords = packed_words(n, kBits);
     for (uint64_t i = tid; i < nwords; i += nthreads) {
-      uint32_t w = 0u;  // four ACC bytes
-      if (P.poison && ((P.poison - 1) >> 2) == i) w = kRsvd << (((P.poison - 1) & 3u) << 3);
+      uint32_t w = 0u;  // every field ACC
+      if (P.poison && (P.poison - 1) / per == i) w = kRsvd << (((P.poison - 1) % per) * kBits);
       P.state[i] = w;
     }
     for (uint64_t v = tid; v < n; v += nthreads) P.mate[v] = kNone;
@@ -50,13 +51,14 @@ __global__ void prepare_kernel(SweepParams P, uint64_t* graph_pairs, uint64_t nu
     P.part[2 * u + 1] = d - rows;
   }
   for (uint64_t g = tid; g < num_graphs && graph_pairs; g += nthreads) graph_pairs[g] = 0;
+  if (P.stats && tid < kStCount) P.stats[tid] = 0ull;
   if (tid == 0) {
     *P.work = 0ull;
     *P.err = 0u;
   }
 }
 
-template <class S>
+template <class S, bool kStats = false>
 __global__ void __launch_bounds__(512, 3) sweep_kernel(SweepParams P) {
   const unsigned lane = threadIdx.x & 31u;
   const S s(P);
@@ -69,7 +71,7 @@ __global__ void __launch_bounds__(512, 3) sweep_kernel(SweepParams P) {
     const int64_t row0 = P.part[2 * w];
     const int64_t e_begin = P.part[2 * w + 1];
     const int64_t e_end = P.part[2 * w + 3];
-    if (e_begin < e_end) sweep_unit(s, P, row0, e_begin, e_end, lane, pol);
+    if (e_begin < e_end) sweep_unit<S, kStats>(s, P, row0, e_begin, e_end, lane, pol);
     if ((w & 15) == 0) {  // stop handing out work once an error is recorded
       uint32_t e = 0;
       if (lane == 0) e = ld_relaxed(P.err);
@@ -123,58 +125,67 @@ __global__ void graph_pairs_kernel(const uint32_t* __restrict__ mate,
 
 }  // namespace
 
-int sweep_blocks_per_sm(bool word, int block_threads) {
+// run F with the state type for `bits` (2, 8 or 32)
+#define SKP_DISPATCH_STATE(bits, F) \
+  ((bits) == 32 ? F(WordState, 32) : (bits) == 2 ? F(TwoBitState, 2) : F(ByteState, 8))
+
+int sweep_blocks_per_sm(int bits, int block_threads) {
   int b = 0;
-  cudaError_t e = word ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_kernel<WordState>, block_threads, 0)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_kernel<ByteState>, block_threads, 0);
+#define OCC(S, B) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_kernel<S>, block_threads, 0)
+  cudaError_t e = SKP_DISPATCH_STATE(bits, OCC);
+#undef OCC
   if (e != cudaSuccess || b < 1) return 1;
   return b;
 }
 
-cudaError_t launch_prepare(const SweepParams& P, bool word, int grid, cudaStream_t s,
+cudaError_t launch_prepare(const SweepParams& P, int bits, int grid, cudaStream_t s,
                            uint64_t* graph_pairs_zero, uint64_t num_graphs) {
-  if (word)
-    prepare_kernel<true><<<grid, 256, 0, s>>>(P, graph_pairs_zero, num_graphs);
-  else
-    prepare_kernel<false><<<grid, 256, 0, s>>>(P, graph_pairs_zero, num_graphs);
+#define L(S, B) (prepare_kernel<B><<<grid, 256, 0, s>>>(P, graph_pairs_zero, num_graphs), 0)
+  SKP_DISPATCH_STATE(bits, L);
+#undef L
   return cudaGetLastError();
 }
 
-cudaError_t launch_sweep(const SweepParams& P, bool word, int grid, int block, cudaStream_t s) {
+cudaError_t launch_sweep(const SweepParams& P, int bits, int grid, int block, cudaStream_t s) {
   if (block > 512 || block < 32 || block % 32) return cudaErrorInvalidValue;
-  if (word)
-    sweep_kernel<WordState><<<grid, block, 0, s>>>(P);
-  else
-    sweep_kernel<ByteState><<<grid, block, 0, s>>>(P);
+  if (P.stats) {
+#define L(S, B) (sweep_kernel<S, true><<<grid, block, 0, s>>>(P), 0)
+    SKP_DISPATCH_STATE(bits, L);
+#undef L
+  } else {
+#define L(S, B) (sweep_kernel<S><<<grid, block, 0, s>>>(P), 0)
+    SKP_DISPATCH_STATE(bits, L);
+#undef L
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_serial(const SweepParams& P, bool word, cudaStream_t s) {
-  if (word)
-    serial_kernel<WordState><<<1, 1, 0, s>>>(P);
-  else
-    serial_kernel<ByteState><<<1, 1, 0, s>>>(P);
+cudaError_t launch_serial(const SweepParams& P, int bits, cudaStream_t s) {
+#define L(S, B) (serial_kernel<S><<<1, 1, 0, s>>>(P), 0)
+  SKP_DISPATCH_STATE(bits, L);
+#undef L
   return cudaGetLastError();
 }
 
-cudaError_t launch_serial_batched(const SweepParams& P, bool word, cudaStream_t s) {
+cudaError_t launch_serial_batched(const SweepParams& P, int bits, cudaStream_t s) {
   const unsigned grid = (unsigned)((P.num_graphs + 127) / 128);
   if (grid == 0) return cudaSuccess;
-  if (word)
-    serial_batched_kernel<WordState><<<grid, 128, 0, s>>>(P);
-  else
-    serial_batched_kernel<ByteState><<<grid, 128, 0, s>>>(P);
+#define L(S, B) (serial_batched_kernel<S><<<grid, 128, 0, s>>>(P), 0)
+  SKP_DISPATCH_STATE(bits, L);
+#undef L
   return cudaGetLastError();
 }
 
-void get_batched_kernels(bool word, bool serial, const void** prepare, const void** sweep,
+void get_batched_kernels(int bits, bool serial, const void** prepare, const void** sweep,
                          const void** pairs) {
-  *prepare = word ? (const void*)prepare_kernel<true> : (const void*)prepare_kernel<false>;
-  if (serial)
-    *sweep = word ? (const void*)serial_batched_kernel<WordState>
-                  : (const void*)serial_batched_kernel<ByteState>;
-  else
-    *sweep = word ? (const void*)sweep_kernel<WordState> : (const void*)sweep_kernel<ByteState>;
+#define PK(S, B) (const void*)prepare_kernel<B>
+#define SB(S, B) (const void*)serial_batched_kernel<S>
+#define SW(S, B) (const void*)sweep_kernel<S>
+  *prepare = SKP_DISPATCH_STATE(bits, PK);
+  *sweep = serial ? SKP_DISPATCH_STATE(bits, SB) : SKP_DISPATCH_STATE(bits, SW);
+#undef PK
+#undef SB
+#undef SW
   *pairs = (const void*)graph_pairs_kernel;
 }
 

@@ -60,7 +60,7 @@ __device__ __forceinline__ int count_le(int rel, int p) {
 // read in chunks of up to 128 (one aligned 128-bit load per lane); the state
 // of the row at the head of each chunk is re-read alongside, so a long row
 // matched by another warp is left after at most one more chunk.
-template <class S>
+template <class S, bool kStats = false>
 __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int64_t row0,
                                            int64_t pos, const int64_t e_end, const unsigned lane,
                                            const uint64_t pol_stream) {
@@ -89,6 +89,7 @@ __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int
       my_end = in ? __ldg(P.offsets + r + 1) : INT64_MAX;
       my_st = in ? s.peek((uint32_t)r) : 0u;
       mchd = __ballot_sync(kFull, !in || S::matched(my_st, (uint32_t)r));
+      if (kStats && lane == 0) atomicAdd(P.stats + kStWindows, 1ull);
       continue;
     }
     const int k1 = __ffs(open) - 1;
@@ -105,6 +106,10 @@ __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int
     // chunk-relative 32-bit coordinates: entry base+p, p in [lo_r, hi_r)
     const int lo_r = (int)(pos - base);
     const int hi_r = (int)(cend - base);
+    if (kStats && lane == 0) {
+      atomicAdd(P.stats + kStChunks, 1ull);
+      atomicAdd(P.stats + kStEntries, (unsigned long long)(hi_r - lo_r));
+    }
     const int64_t rel64 = my_end - base;
     const int rel = rel64 < 0 ? -1 : (rel64 > 129 ? 129 : (int)rel64);
 
@@ -181,7 +186,7 @@ __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int
       unsigned done = 0u;
       if (have && (int)lane == leader) {
         cand &= ~(1u << j);
-        if (resolve_edge(s, key, pick4(y, j), pick4(rx, j), pick4(ry, j), P))
+        if (resolve_edge<S, kStats>(s, key, pick4(y, j), pick4(rx, j), pick4(ry, j), P))
           done = 1u << (key - (uint32_t)wbase);
       }
       done = __reduce_or_sync(kFull, done);  // rows that are now matched

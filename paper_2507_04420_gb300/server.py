@@ -29,10 +29,12 @@ __all__ = ["Request", "Server", "device_bytes", "plan_admission"]
 
 
 def device_bytes(n: int, nnz: int) -> int:
-    """Device memory a request holds while resident: offsets, neighbour ids,
-    mate/state, rounded up to the allocator's 512-byte granules."""
+    """Device memory a request holds while resident: offsets, neighbour ids and
+    mate, plus its share of the launch scratch (packed states, partition and
+    unit tables, the checker's marks), rounded up to 512-byte granules."""
     r = lambda b: (b + 511) // 512 * 512
-    return r(8 * (n + 1)) + r(4 * max(nnz, 1)) + r(4 * max(n, 1))
+    scratch = (n // 4 + 8) + n + 24 * ((n + nnz) // 1024 + 2)
+    return r(8 * (n + 1)) + r(4 * max(nnz, 1)) + r(4 * max(n, 1)) + r(scratch)
 
 
 def plan_admission(sizes: Sequence[int], used: int, budget: int, max_graphs: int) -> Tuple[int, int]:
@@ -77,13 +79,15 @@ class Request:
 
 
 class Server:
-    def __init__(self, device=None, memory_bytes: Optional[int] = None, reserve_bytes: int = 2 << 30,
-                 max_graphs_per_tick: int = 4096, status_bits: int = 32, grain: int = 2048,
-                 serial: bool = False, validate: bool = True, slots: int = 2):
+    def __init__(self, device=None, memory_bytes: Optional[int] = None, reserve_bytes: int = 8 << 30,
+                 max_graphs_per_tick: int = 4096, max_bytes_per_tick: int = 32 << 30,
+                 status_bits: int = 32, grain: int = 2048, serial: bool = False,
+                 validate: bool = True, slots: int = 2):
         self.dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         free, _ = torch.cuda.mem_get_info(self.dev)
         self.budget = memory_bytes if memory_bytes is not None else max(0, free - reserve_bytes)
         self.max_graphs = max_graphs_per_tick
+        self.max_tick_bytes = max_bytes_per_tick
         self.validate = validate
         self.opts = options(status_bits=status_bits, grain=grain, serial=int(serial), nosync=1)
         self.h2d = torch.cuda.Stream(self.dev)
@@ -110,6 +114,11 @@ class Server:
             rid = self._rid
             self._rid += 1
         req = Request(rid, offsets, nbrs)
+        if self.error is not None:
+            req.error = self.error
+            req.done_t = time.perf_counter()
+            req._event.set()
+            return req
         if req._bytes > self.budget:
             req.error = MemoryError(f"request needs {req._bytes} device bytes, budget {self.budget}")
             req.done_t = time.perf_counter()
@@ -200,8 +209,12 @@ class Server:
                 while inflight and self._complete(inflight[0]):
                     inflight.popleft()
                     busy = True
-                k, add = plan_admission([r._bytes for r in pending], self.used, self.budget,
+                staged_bytes = sum(r._bytes for r in staged)
+                room = min(self.budget, self.used + self.max_tick_bytes - staged_bytes)
+                k, add = plan_admission([r._bytes for r in pending], self.used, room,
                                         self.max_graphs - len(staged))
+                if k == 0 and not staged and not inflight and pending and pending[0]._bytes > self.max_tick_bytes:
+                    k, add = 1, pending[0]._bytes  # one request larger than a tick runs alone
                 for _ in range(k):
                     r = pending.popleft()
                     self._admit(r)
@@ -216,8 +229,16 @@ class Server:
                     return
                 if not busy:
                     time.sleep(50e-6)
-        except BaseException as e:  # surface worker failures to close() and to waiters
+        except BaseException as e:  # surface worker failures to close() and to every waiter
             self.error = e
-            for r in list(pending) + staged + [r for t in inflight for r in t[1]]:
+            self._closing = True
+            left = list(pending) + staged + [r for t in inflight for r in t[1]]
+            while True:
+                try:
+                    left.append(self._inbox.get_nowait())
+                except queue.Empty:
+                    break
+            for r in left:
                 r.error = e
+                r.done_t = time.perf_counter()
                 r._event.set()

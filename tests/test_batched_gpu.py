@@ -43,7 +43,7 @@ def test_batched_serial_equals_sgmm_per_graph(skp, batch):
     off, nb = packed.csr.offsets.numpy(), packed.csr.nbrs.numpy()
     ref_union, _ = oracle.sgmm(off, nb)
     with skp.Graph(d.offsets, d.nbrs) as h:
-        for bits in (8, 32):
+        for bits in (2, 8, 32):
             for use_graph in (0, 1):
                 mate, gp = h.batched(vb, eb, graph_pairs=True, serial=1, status_bits=bits,
                                      use_graph=use_graph)
@@ -56,7 +56,7 @@ def test_batched_serial_equals_sgmm_per_graph(skp, batch):
                     assert int(gp[k]) == len(ref_pairs)
 
 
-@pytest.mark.parametrize("bits", [8, 32])
+@pytest.mark.parametrize("bits", [2, 8, 32])
 @pytest.mark.parametrize("use_graph", [0, 1])
 def test_batched_parallel_valid(skp, batch, bits, use_graph):
     graphs, packed = batch
@@ -102,6 +102,6 @@ def test_autotune_picks_a_valid_setting(skp, batch):
     vb, eb = packed.vbase.cuda(), packed.ebase.cuda()
     with skp.Graph(d.offsets, d.nbrs) as h:
         o = h.autotune_batched(vb, eb)
-        assert o.status_bits in (8, 32) and o.grain in (1024, 2048, 4096, 8192)
+        assert o.status_bits in (2, 8, 32) and o.grain in (1024, 2048, 4096, 8192)
         mate = h.batched(vb, eb, opts=o)
         assert h.validate(mate).flags == 0

@@ -64,7 +64,7 @@ SMALL = {
 }
 
 
-@pytest.mark.parametrize("bits", [8, 32])
+@pytest.mark.parametrize("bits", [2, 8, 32])
 @pytest.mark.parametrize("name", sorted(SMALL))
 def test_serial_equals_sgmm(skp, name, bits):
     csr = SMALL[name]()
@@ -75,7 +75,7 @@ def test_serial_equals_sgmm(skp, name, bits):
     assert_parity(vr, vd)
 
 
-@pytest.mark.parametrize("bits", [8, 32])
+@pytest.mark.parametrize("bits", [2, 8, 32])
 @pytest.mark.parametrize("name", sorted(SMALL))
 def test_parallel_valid_and_verdicts_identical(skp, name, bits):
     csr = SMALL[name]()
@@ -94,7 +94,7 @@ def test_parallel_valid_and_verdicts_identical(skp, name, bits):
             assert m.tolist() == [v ^ 1 for v in range(100)]
 
 
-@pytest.mark.parametrize("bits", [8, 32])
+@pytest.mark.parametrize("bits", [2, 8, 32])
 def test_er_100k_1m(skp, bits):
     """Erdos-Renyi n=100,000, m=1,000,000 (2M directed entries)."""
     csr = gg.erdos_renyi(100_000, 1_000_000, seed=1)
@@ -108,7 +108,7 @@ def test_er_100k_1m(skp, bits):
         assert 2 * len(p) >= len(ref_pairs)
 
 
-@pytest.mark.parametrize("bits", [8, 32])
+@pytest.mark.parametrize("bits", [2, 8, 32])
 @pytest.mark.parametrize("block", [32, 256, 512])
 def test_launch_shapes(skp, bits, block):
     csr = gg.rmat(14, 16, seed=9)
@@ -131,7 +131,7 @@ def test_loops_unsorted_rows_and_ragged_tail(skp):
     # self-loops, rows in arbitrary order, nnz = 13 (not a multiple of 4)
     csr = _manual(6, [[0, 3, 1], [0, 1, 2], [5, 1], [0, 3, 4], [3], [2]])
     ref_mate, _ = oracle.sgmm(csr.offsets.numpy(), csr.nbrs.numpy())
-    for bits in (8, 32):
+    for bits in (2, 8, 32):
         m, p, vr, vd = run(skp, csr, status_bits=bits, serial=1)
         assert np.array_equal(m, ref_mate)
         assert_parity(vr, vd)
@@ -150,7 +150,7 @@ def test_edges_stored_once(skp):
     off2 = np.zeros(g.n + 1, dtype=np.int64)
     off2[1:] = np.cumsum(cnt)
     csr = gg.CSR(torch.from_numpy(off2), torch.from_numpy(nb[keep].copy()))
-    for bits in (8, 32):
+    for bits in (2, 8, 32):
         m, p, vr, vd = run(skp, csr, status_bits=bits)
         assert_parity(vr, vd)
         ref_mate, _ = oracle.sgmm(off2, nb[keep])
@@ -165,7 +165,7 @@ def test_empty_rows_and_tiny_graphs(skp):
     v = torch.tensor([1, 2, 501, 502, 503, 2999, 1500, 1000], dtype=torch.int64)
     csr = gg.from_edges(n, u, v)
     ref_mate, _ = oracle.sgmm(csr.offsets.numpy(), csr.nbrs.numpy())
-    for bits in (8, 32):
+    for bits in (2, 8, 32):
         m, p, vr, vd = run(skp, csr, status_bits=bits, serial=1)
         assert np.array_equal(m, ref_mate)
         for grain in (128, 2048):
@@ -202,7 +202,7 @@ def test_misaligned_and_bad_graphs(skp):
     assert e.value.status == "MM_ERR_ARG"
 
 
-@pytest.mark.parametrize("bits", [8, 32])
+@pytest.mark.parametrize("bits", [2, 8, 32])
 def test_wait_limit_reports_timeout_and_context_survives(skp, bits):
     """A vertex left RESERVED by no thread: every wait on it runs out, the call
     returns MM_ERR_TIMEOUT (no trap, no hang), and the next call is normal."""
@@ -269,7 +269,7 @@ def test_pairs_cap_nosync_and_timing(skp):
         assert np.array_equal(_np(pairs[:k]).reshape(-1, 2)[:, 0], us)
 
 
-@pytest.mark.parametrize("bits", [8, 32])
+@pytest.mark.parametrize("bits", [2, 8, 32])
 def test_contention_shapes_and_rmat22(skp, bits):
     """RMAT scale 22 (ef 16), star with 1M leaves, path of 4M vertices,
     K_{2048,2048} and a 2048x2048 grid: verdicts identical to the oracle's."""
@@ -297,3 +297,22 @@ def test_contention_shapes_and_rmat22(skp, bits):
             assert k == 2048
         del d
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("bits", [2, 8, 32])
+def test_sweep_statistics(skp, bits):
+    """stats=1 counts each successful claim once: matches == pairs in the result;
+    every entry read at most once; conflicts fall in Table II's bins."""
+    for csr in (gg.rmat(14, 16, seed=5), gg.complete_bipartite(64, 64), gg.star(5000)):
+        d = csr.to("cuda")
+        with skp.Graph(d.offsets, d.nbrs) as h:
+            mate = h.skipper(status_bits=bits, stats=1)
+            st = h.stats()
+            v = h.validate(mate)
+            assert v.flags == 0
+            assert st["matches"] == v.n_pairs
+            assert st["matches"] <= st["attempts"]
+            assert 0 < st["entries_read"] <= csr.nnz
+            assert st["conflicted_entries"] == sum(st["hist"])
+            assert st["conflicts"] >= st["conflicted_entries"]
+            assert (st["max_conflicts"] > 0) == (st["conflicted_entries"] > 0)

@@ -40,7 +40,7 @@ def _np(t):
     return t.cpu().numpy().view(np.uint32)
 
 
-@pytest.mark.parametrize("bits", [8, 32])
+@pytest.mark.parametrize("bits", [2, 8, 32])
 def test_multi_serial_equals_sgmm_and_parallel_valid(skp, graphs, bits):
     dev = [g.to("cuda") for g in graphs]
     m = skp.Multi()
