@@ -93,7 +93,7 @@ def measured_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("state.cuh", "sweep.cu"):
+    for f in ("state.cuh", "walk.cuh", "sweep.cu"):
         with open(os.path.join(ROOT, "paper_2507_04420_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
