@@ -82,6 +82,23 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(x: float, dist=None) -> float:
+    """Largest value of x over all ranks (x itself without a process group);
+    CUDA tensors under NCCL, host tensors under gloo."""
+    if dist is None or not dist.is_initialized():
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gedges(world: int, entries_per_rank: int, seconds: float) -> float:
+    """Whole-job GEdges/s: every rank's entries over the slowest rank's time."""
+    return world * entries_per_rank / seconds / 1e9
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -469,11 +486,8 @@ def run_ours(args):
     v_end = h.validate(mate)
     if v_end.flags != 0:
         raise SystemExit(f"invalid matching after timing: {v_end.as_dict()}")
-    if dist:
-        t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * nnz / (ms_step * 1e-3) / 1e9
+    ms_step = max_over_ranks(ms_step, dist)
+    value = job_gedges(world, nnz, ms_step * 1e-3)
 
     # roofline of the dominant kernel (the sweep): algorithmic bytes = CSR once
     peak, peak_kind = measured_peaks()
@@ -500,11 +514,8 @@ def run_ours(args):
         for _ in range(args.e2e_steps):
             sess.run(h_off, h_nb, h_mate, status_bits=args.bits, grain=args.grain)
         e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-        if dist:
-            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * nnz / e2e_s / 1e9, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
+        e2e_s = max_over_ranks(e2e_s, dist)
+        e2e = {"value": job_gedges(world, nnz, e2e_s), "unit": UNIT, "ms_per_step": e2e_s * 1e3,
                "h2d_bytes_per_step": 8 * (n + 1) + 4 * nnz, "d2h_bytes_per_step": 4 * n,
                "how": "HostSession.run: pinned host CSR -> device, mm_skipper, mate -> pinned host, sync"}
         sess.close()
