@@ -24,23 +24,43 @@ namespace skp {
 
 namespace {
 
+// Fill p[0, count) with `value`, except p[special] = special_value (special
+// may be out of range): 128-bit stores for the aligned body, plain stores for
+// the ragged ends.  The element `special` is written by the store covering it.
+__device__ __forceinline__ void fill_words(uint32_t* p, uint64_t count, uint32_t value, uint64_t special,
+                                           uint32_t special_value, uint64_t tid, uint64_t nthreads) {
+  const uint64_t head = ((16u - (reinterpret_cast<uintptr_t>(p) & 15u)) & 15u) / 4u;
+  const uint64_t h = head < count ? head : count;
+  for (uint64_t i = tid; i < h; i += nthreads) p[i] = i == special ? special_value : value;
+  const uint64_t body = (count - h) / 4;
+  uint4* q = reinterpret_cast<uint4*>(p + h);
+  for (uint64_t i = tid; i < body; i += nthreads) {
+    const uint64_t e = h + 4 * i;
+    uint4 v = make_uint4(value, value, value, value);
+    if (special - e < 4) {
+      const uint32_t k = (uint32_t)(special - e);
+      if (k == 0) v.x = special_value; else if (k == 1) v.y = special_value;
+      else if (k == 2) v.z = special_value; else v.w = special_value;
+    }
+    q[i] = v;
+  }
+  for (uint64_t i = h + 4 * body + tid; i < count; i += nthreads) p[i] = i == special ? special_value : value;
+}
+
 template <int kBits>
 __global__ void prepare_kernel(SweepParams P, uint64_t* graph_pairs, uint64_t num_graphs) {
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t n = P.n;
+  const uint64_t none = ~0ull;
   if (kBits == 32) {
-    for (uint64_t v = tid; v < n; v += nthreads)
-      P.state[v] = (P.poison && v == P.poison - 1) ? kWRsvd : kWAcc;
+    fill_words(P.state, n, kWAcc, P.poison ? P.poison - 1 : none, kWRsvd, tid, nthreads);
   } else {
     constexpr uint64_t per = 32 / kBits;
-    const uint64_t nwords = packed_words(n, kBits);
-    for (uint64_t i = tid; i < nwords; i += nthreads) {
-      uint32_t w = 0u;  // every field ACC
-      if (P.poison && (P.poison - 1) / per == i) w = kRsvd << (((P.poison - 1) % per) * kBits);
-      P.state[i] = w;
-    }
-    for (uint64_t v = tid; v < n; v += nthreads) P.mate[v] = kNone;
+    const uint64_t pv = P.poison ? P.poison - 1 : none;
+    fill_words(P.state, packed_words(n, kBits), 0u, P.poison ? pv / per : none,
+               P.poison ? kRsvd << ((pv % per) * kBits) : 0u, tid, nthreads);
+    fill_words(P.mate, n, kNone, none, kNone, tid, nthreads);
   }
   const int64_t total = (int64_t)(n + P.nnz);
   for (uint64_t u = tid; u <= P.units; u += nthreads) {

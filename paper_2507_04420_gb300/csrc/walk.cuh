@@ -130,10 +130,7 @@ __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int
     }
     const uint32_t x1 = (uint32_t)(wbase + k1);
     uint32_t head = 0;
-    if (lane == 0) head = s.peek(x1);
-    head = __shfl_sync(kFull, head, 0);
-    if (S::matched(head, x1)) mchd |= 1u << k1;
-    if (lane == (unsigned)k1) my_st = head;
+    if (lane == 0) head = s.peek(x1);  // consumed after the row search, so both loads overlap it
 
     // row of each entry within the window
     int k[4];
@@ -146,6 +143,9 @@ __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int
       k[1] = k[0];
       k[2] = k[0];
     }
+    head = __shfl_sync(kFull, head, 0);
+    if (S::matched(head, x1)) mchd |= 1u << k1;
+    if (lane == (unsigned)k1) my_st = head;
     // words holding the row states, from the window snapshot
     uint32_t rx[4], xs[4];
 #pragma unroll
