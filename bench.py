@@ -385,8 +385,9 @@ def run_served(args, skp):
         return t0, finish()
 
     srv = Server(status_bits=args.bits, grain=2048)
+    outs = [torch.empty(x[2], dtype=torch.int32, pin_memory=True) for x in pool]  # result buffers, reused
     reqs = []
-    t0, _ = run_trace(lambda p, at: reqs.append(srv.submit(pool[p][0], pool[p][1])),
+    t0, _ = run_trace(lambda p, at: reqs.append(srv.submit(pool[p][0], pool[p][1], outs[p])),
                       lambda: [r.wait(600) for r in reqs])
     srv.close()   # raises the worker's error, if any
     if any(r.done_t is None for r in reqs):
@@ -399,7 +400,8 @@ def run_served(args, skp):
                      "mean_graphs_per_launch": statistics.mean(srv.tick_sizes), "invalid": bad,
                      "how": "server.Server: admission by device-memory budget, H2D on a copy stream, "
                             "one mm_skipper_multi launch per tick on two alternating compute streams, "
-                            "mm_validate_multi before completion, D2H on a second copy stream"}
+                            "mm_validate_multi before completion, D2H on a second copy stream into "
+                            "a result buffer per pool graph (reused, as the serial run does)"}
     # serial plain: one request at a time through the plain API, in arrival order
     sess = skp.HostSession(max(x[2] for x in pool), max(x[3] for x in pool))
     lat2 = []

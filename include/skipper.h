@@ -289,6 +289,10 @@ mm_status mm_autotune_batched(mm_graph *g, uint64_t num_graphs, const int64_t *d
  * MM_ERR_UNSUPPORTED.  Waits for the GPU unless nosync (then mm_multi_sync).
  * mm_validate_multi: the exact checker (counting rules above, without a pair
  * list) for every graph at once; h_out[k] is graph k's verdict.  Synchronous.
+ * mm_validate_multi_async enqueues the same check on the stream (it may follow
+ * an mm_skipper_multi call on the same stream at once: the two use separate
+ * tables); once the stream has passed it, mm_multi_verdicts writes the
+ * verdicts of that check (num_graphs must match).
  */
 typedef struct mm_graph_desc {
     uint64_t n;
@@ -306,6 +310,9 @@ mm_status mm_skipper_multi(mm_multi *m, uint64_t num_graphs, const mm_graph_desc
 mm_status mm_multi_sync(mm_multi *m, void *cuda_stream);
 mm_status mm_validate_multi(mm_multi *m, uint64_t num_graphs, const mm_graph_desc *h_descs,
                             mm_verdict *h_out, void *cuda_stream);
+mm_status mm_validate_multi_async(mm_multi *m, uint64_t num_graphs, const mm_graph_desc *h_descs,
+                                  void *cuda_stream);
+mm_status mm_multi_verdicts(mm_multi *m, uint64_t num_graphs, mm_verdict *h_out);
 mm_status mm_multi_destroy(mm_multi *m);
 
 /* Release the handle's scratch.  Does not touch the borrowed CSR. */

@@ -250,6 +250,18 @@ class Multi:
                "mm_validate_multi")
         return [out[i] for i in range(len(graphs))]
 
+    def validate_async(self, graphs, stream=None):
+        """Enqueue the checker for these graphs on the stream (after a run on it)."""
+        arr = self._descs(graphs)
+        _check(lib.mm_validate_multi_async(self._h, len(graphs), arr, _stream_ptr(stream)),
+               "mm_validate_multi_async")
+
+    def verdicts(self, count: int):
+        """Verdicts of the last validate_async, once its stream has passed it."""
+        out = (Verdict * max(1, count))()
+        _check(lib.mm_multi_verdicts(self._h, count, out), "mm_multi_verdicts")
+        return [out[i] for i in range(count)]
+
     def close(self):
         if getattr(self, "_h", None):
             lib.mm_multi_destroy(self._h)

@@ -170,6 +170,8 @@ SYMBOLS = [
     ("mm_skipper_multi", _I, [_P, _U64, ctypes.POINTER(GraphDesc), ctypes.POINTER(Options), _P]),
     ("mm_multi_sync", _I, [_P, _P]),
     ("mm_validate_multi", _I, [_P, _U64, ctypes.POINTER(GraphDesc), ctypes.POINTER(Verdict), _P]),
+    ("mm_validate_multi_async", _I, [_P, _U64, ctypes.POINTER(GraphDesc), _P]),
+    ("mm_multi_verdicts", _I, [_P, _U64, ctypes.POINTER(Verdict)]),
     ("mm_multi_destroy", _I, [_P]),
     ("mm_destroy", _I, [_P]),
     ("mm_skipper_static", _I, [_U64, _U64, _P, _P, _P, ctypes.POINTER(Options), _P]),

@@ -246,14 +246,21 @@ __global__ void multi_validate_kernel(MultiParams M) {
   }
 }
 
+// Grow a device buffer to at least `want` elements, ordered on the call's
+// stream (cudaFreeAsync / cudaMallocAsync), so growing never waits for the
+// whole device; capacity doubles so growth is rare.
 template <class T>
-cudaError_t grow(T** p, uint64_t* cap, uint64_t want) {
+cudaError_t grow(T** p, uint64_t* cap, uint64_t want, cudaStream_t s) {
   if (*p && *cap >= want) return cudaSuccess;
-  if (*p) cudaFree(*p);
+  uint64_t n = *cap ? *cap : 64;
+  while (n < want) n *= 2;
+  if (*p) {
+    cudaError_t e = cudaFreeAsync(*p, s);
+    if (e != cudaSuccess) return e;
+  }
   *p = nullptr;
   *cap = 0;
-  const uint64_t n = want + want / 4 + 64;
-  cudaError_t e = cudaMalloc(p, n * sizeof(T));
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(p), n * sizeof(T), s);
   if (e == cudaSuccess) *cap = n;
   return e;
 }
@@ -280,13 +287,14 @@ mm_status mfail(mm_status st, const char* fmt, ...) {
 }  // namespace
 }  // namespace skp
 
-struct mm_multi {
-  int device = 0;
-  int num_sms = 0;
-  // device tables: [desc G | ubase G+1 | vbase G+1 | sbase G+1]
+// Device tables of one call ([desc G | ubase G+1 | vbase G+1 | sbase G+1]),
+// their pinned staging copy and the partition built on them.  The sweep and
+// the checker have one set each, so a checker enqueued right behind a sweep
+// never waits for the sweep's staging copy.
+struct TableSet {
   unsigned char* tables = nullptr;
   uint64_t tables_cap = 0;
-  unsigned char* staging = nullptr;  // pinned host copy of the tables
+  unsigned char* staging = nullptr;    // pinned host copy of the tables
   uint64_t staging_cap = 0;
   cudaEvent_t staging_free = nullptr;  // the last copy out of `staging` has finished
   bool staging_pending = false;
@@ -294,6 +302,12 @@ struct mm_multi {
   uint64_t part_cap = 0;
   uint32_t* gid = nullptr;
   uint64_t gid_cap = 0;
+};
+
+struct mm_multi {
+  int device = 0;
+  int num_sms = 0;
+  TableSet sweep, check;
   uint32_t* pool = nullptr;
   uint64_t pool_cap = 0;
   unsigned long long* counters = nullptr;
@@ -304,6 +318,7 @@ struct mm_multi {
   uint32_t* h_err = nullptr;           // pinned
   unsigned long long* h_counters = nullptr;
   uint64_t h_counters_cap = 0;
+  uint64_t checked_graphs = 0;         // graphs of the last enqueued check
 };
 
 namespace skp {
@@ -316,7 +331,7 @@ struct Layout {
   uint64_t total_vertices = 0, total_words = 0;
 };
 
-mm_status stage_tables(mm_multi* m, uint64_t G, const mm_graph_desc* h, uint64_t grain, int bits,
+mm_status stage_tables(TableSet* m, uint64_t G, const mm_graph_desc* h, uint64_t grain, int bits,
                        cudaStream_t s, Layout* L) {
   L->off_ubase = G * sizeof(mm_graph_desc);
   L->off_vbase = L->off_ubase + (G + 1) * 8;
@@ -330,11 +345,12 @@ mm_status stage_tables(mm_multi* m, uint64_t G, const mm_graph_desc* h, uint64_t
     if (m->staging) cudaFreeHost(m->staging);
     m->staging = nullptr;
     m->staging_cap = 0;
-    const uint64_t cap = L->bytes + L->bytes / 4 + 256;
+    uint64_t cap = m->staging_cap ? m->staging_cap : 4096;
+    while (cap < L->bytes) cap *= 2;
     MTRY(cudaMallocHost(&m->staging, cap));
     m->staging_cap = cap;
   }
-  MTRY(grow(&m->tables, &m->tables_cap, L->bytes));
+  MTRY(grow(&m->tables, &m->tables_cap, L->bytes, s));
   memcpy(m->staging, h, G * sizeof(mm_graph_desc));
   uint64_t* ub = reinterpret_cast<uint64_t*>(m->staging + L->off_ubase);
   uint64_t* vb = reinterpret_cast<uint64_t*>(m->staging + L->off_vbase);
@@ -354,16 +370,17 @@ mm_status stage_tables(mm_multi* m, uint64_t G, const mm_graph_desc* h, uint64_t
   return MM_OK;
 }
 
-MultiParams params(mm_multi* m, uint64_t G, const Layout& L, uint64_t grain, uint64_t spin) {
+MultiParams params(mm_multi* m, const TableSet& t, uint64_t G, const Layout& L, uint64_t grain,
+                   uint64_t spin) {
   MultiParams M{};
   M.num_graphs = G;
-  M.desc = reinterpret_cast<const mm_graph_desc*>(m->tables);
-  M.ubase = reinterpret_cast<const uint64_t*>(m->tables + L.off_ubase);
-  M.vbase = reinterpret_cast<const uint64_t*>(m->tables + L.off_vbase);
-  M.sbase = reinterpret_cast<const uint64_t*>(m->tables + L.off_sbase);
+  M.desc = reinterpret_cast<const mm_graph_desc*>(t.tables);
+  M.ubase = reinterpret_cast<const uint64_t*>(t.tables + L.off_ubase);
+  M.vbase = reinterpret_cast<const uint64_t*>(t.tables + L.off_vbase);
+  M.sbase = reinterpret_cast<const uint64_t*>(t.tables + L.off_sbase);
   M.state_pool = m->pool;
-  M.part = m->part;
-  M.gid = m->gid;
+  M.part = t.part;
+  M.gid = t.gid;
   M.units = L.units;
   M.grain = grain;
   M.work = m->ctrl;
@@ -400,7 +417,8 @@ mm_status mm_multi_create(mm_multi** out) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device);
   if (e == cudaSuccess) e = cudaMalloc(&m->ctrl, 16 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMallocHost(&m->h_err, 64);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->staging_free, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->sweep.staging_free, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->check.staging_free, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     mm_multi_destroy(m);
     return mfail(MM_ERR_CUDA, "mm_multi_create: %s", cudaGetErrorString(e));
@@ -432,11 +450,11 @@ mm_status mm_skipper_multi(mm_multi* m, uint64_t num_graphs, const mm_graph_desc
                                      "available in multi-graph calls");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   Layout L;
-  if ((st = stage_tables(m, num_graphs, h_descs, grain, (int)bits, s, &L)) != MM_OK) return st;
-  MTRY(grow(&m->part, &m->part_cap, 2 * (L.units + 1)));
-  MTRY(grow(&m->gid, &m->gid_cap, L.units + 1));
-  if (!word) MTRY(grow(&m->pool, &m->pool_cap, L.total_words + 1));
-  const MultiParams M = params(m, num_graphs, L, grain, o->spin_limit ? o->spin_limit : (1ull << 20));
+  if ((st = stage_tables(&m->sweep, num_graphs, h_descs, grain, (int)bits, s, &L)) != MM_OK) return st;
+  MTRY(grow(&m->sweep.part, &m->sweep.part_cap, 2 * (L.units + 1), s));
+  MTRY(grow(&m->sweep.gid, &m->sweep.gid_cap, L.units + 1, s));
+  if (!word) MTRY(grow(&m->pool, &m->pool_cap, L.total_words + 1, s));
+  const MultiParams M = params(m, m->sweep, num_graphs, L, grain, o->spin_limit ? o->spin_limit : (1ull << 20));
 
   const int prep_grid = m->num_sms * 8;
   if (word) multi_prepare_kernel<true><<<prep_grid, 256, 0, s>>>(M);
@@ -475,28 +493,33 @@ mm_status mm_multi_sync(mm_multi* m, void* cuda_stream) {
   return MM_OK;
 }
 
-mm_status mm_validate_multi(mm_multi* m, uint64_t num_graphs, const mm_graph_desc* h_descs,
-                            mm_verdict* h_out, void* cuda_stream) {
-  if (!m || !h_out) return mfail(MM_ERR_ARG, "null argument");
+mm_status mm_validate_multi_async(mm_multi* m, uint64_t num_graphs, const mm_graph_desc* h_descs,
+                                  void* cuda_stream) {
+  if (!m) return mfail(MM_ERR_ARG, "null handle");
+  m->checked_graphs = 0;
   if (!num_graphs) return MM_OK;
   if (!h_descs) return mfail(MM_ERR_ARG, "null descriptors");
   mm_status st = check_descs(num_graphs, h_descs);
   if (st != MM_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   Layout L;
-  if ((st = stage_tables(m, num_graphs, h_descs, kCheckGrain, 32, s, &L)) != MM_OK) return st;
-  MTRY(grow(&m->counters, &m->counters_cap, num_graphs * C_N));
-  MTRY(grow(&m->found, &m->found_cap, L.total_vertices + 16));
-  MTRY(grow(&m->part, &m->part_cap, 2 * (L.units + 1)));
-  MTRY(grow(&m->gid, &m->gid_cap, L.units + 1));
+  if ((st = stage_tables(&m->check, num_graphs, h_descs, kCheckGrain, 32, s, &L)) != MM_OK) return st;
+  MTRY(grow(&m->counters, &m->counters_cap, num_graphs * C_N, s));
+  MTRY(grow(&m->found, &m->found_cap, L.total_vertices + 16, s));
+  MTRY(grow(&m->check.part, &m->check.part_cap, 2 * (L.units + 1), s));
+  MTRY(grow(&m->check.gid, &m->check.gid_cap, L.units + 1, s));
   if (m->h_counters_cap < num_graphs * C_N) {
+    // the previous check's counters may still be on their way into the old buffer
+    MTRY(cudaStreamSynchronize(s));
     if (m->h_counters) cudaFreeHost(m->h_counters);
     m->h_counters = nullptr;
+    uint64_t cap = m->h_counters_cap ? m->h_counters_cap : 64 * C_N;
+    while (cap < num_graphs * C_N) cap *= 2;
     m->h_counters_cap = 0;
-    MTRY(cudaMallocHost(&m->h_counters, num_graphs * C_N * sizeof(unsigned long long)));
-    m->h_counters_cap = num_graphs * C_N;
+    MTRY(cudaMallocHost(&m->h_counters, cap * sizeof(unsigned long long)));
+    m->h_counters_cap = cap;
   }
-  const MultiParams M = params(m, num_graphs, L, kCheckGrain, 1);
+  const MultiParams M = params(m, m->check, num_graphs, L, kCheckGrain, 1);
   const int grid = m->num_sms * 8;
   multi_counters_init_kernel<<<m->num_sms * 4, 256, 0, s>>>(m->counters, num_graphs);
   if (L.total_vertices) {
@@ -510,7 +533,15 @@ mm_status mm_validate_multi(mm_multi* m, uint64_t num_graphs, const mm_graph_des
   MTRY(cudaGetLastError());
   MTRY(cudaMemcpyAsync(m->h_counters, m->counters, num_graphs * C_N * sizeof(unsigned long long),
                        cudaMemcpyDeviceToHost, s));
-  MTRY(cudaStreamSynchronize(s));
+  m->checked_graphs = num_graphs;
+  return MM_OK;
+}
+
+mm_status mm_multi_verdicts(mm_multi* m, uint64_t num_graphs, mm_verdict* h_out) {
+  if (!m || (num_graphs && !h_out)) return mfail(MM_ERR_ARG, "null argument");
+  if (num_graphs != m->checked_graphs)
+    return mfail(MM_ERR_ARG, "%llu verdicts asked, the last check covered %llu graphs",
+                 (unsigned long long)num_graphs, (unsigned long long)m->checked_graphs);
   for (uint64_t g = 0; g < num_graphs; ++g) {
     const unsigned long long* c = m->h_counters + g * C_N;
     mm_verdict v{};
@@ -532,14 +563,25 @@ mm_status mm_validate_multi(mm_multi* m, uint64_t num_graphs, const mm_graph_des
   return MM_OK;
 }
 
+mm_status mm_validate_multi(mm_multi* m, uint64_t num_graphs, const mm_graph_desc* h_descs,
+                            mm_verdict* h_out, void* cuda_stream) {
+  if (!m || (num_graphs && !h_out)) return mfail(MM_ERR_ARG, "null argument");
+  mm_status st = mm_validate_multi_async(m, num_graphs, h_descs, cuda_stream);
+  if (st != MM_OK) return st;
+  MTRY(cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream)));
+  return mm_multi_verdicts(m, num_graphs, h_out);
+}
+
 mm_status mm_multi_destroy(mm_multi* m) {
   if (!m) return MM_OK;
-  if (m->staging_pending && m->staging_free) cudaEventSynchronize(m->staging_free);
-  if (m->staging_free) cudaEventDestroy(m->staging_free);
-  if (m->tables) cudaFree(m->tables);
-  if (m->staging) cudaFreeHost(m->staging);
-  if (m->part) cudaFree(m->part);
-  if (m->gid) cudaFree(m->gid);
+  for (TableSet* t : {&m->sweep, &m->check}) {
+    if (t->staging_pending && t->staging_free) cudaEventSynchronize(t->staging_free);
+    if (t->staging_free) cudaEventDestroy(t->staging_free);
+    if (t->tables) cudaFree(t->tables);
+    if (t->staging) cudaFreeHost(t->staging);
+    if (t->part) cudaFree(t->part);
+    if (t->gid) cudaFree(t->gid);
+  }
   if (m->pool) cudaFree(m->pool);
   if (m->counters) cudaFree(m->counters);
   if (m->found) cudaFree(m->found);

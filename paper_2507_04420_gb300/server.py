@@ -106,14 +106,24 @@ class Server:
         self._thread.start()
 
     # -- client side ------------------------------------------------------------
-    def submit(self, offsets: torch.Tensor, nbrs: torch.Tensor) -> Request:
-        """Queue one graph (host CSR; pinned memory makes the copy asynchronous)."""
+    def submit(self, offsets: torch.Tensor, nbrs: torch.Tensor,
+               mate_out: Optional[torch.Tensor] = None) -> Request:
+        """Queue one graph (host CSR; pinned memory makes the copy asynchronous).
+
+        mate_out: optional host int32 tensor of n entries (pinned for an
+        asynchronous copy) that receives the result; a client that recycles
+        its result buffers keeps pinned allocations out of the serving loop.
+        Without it the server allocates one."""
         if offsets.is_cuda or nbrs.is_cuda:
             raise ValueError("submit host tensors")
+        if mate_out is not None and (mate_out.is_cuda or mate_out.numel() != offsets.numel() - 1
+                                     or mate_out.dtype != torch.int32):
+            raise ValueError("mate_out must be a host int32 tensor of n entries")
         with self._lock:
             rid = self._rid
             self._rid += 1
         req = Request(rid, offsets, nbrs)
+        req.mate = mate_out
         if self.error is not None:
             req.error = self.error
             req.done_t = time.perf_counter()
@@ -157,24 +167,29 @@ class Server:
         multi.run(graphs, stream=stream, opts=self.opts)
         swept = torch.cuda.Event()
         swept.record(stream)
+        if self.validate:  # the checker runs behind the pass, on the same stream
+            multi.validate_async(graphs, stream=stream)
+        checked = torch.cuda.Event()
+        checked.record(stream)
         for r in batch:  # the device tensors were made on the copy stream; they are used here too
             for t in r._dev:
                 t.record_stream(stream)
         self.d2h.wait_event(swept)
         with torch.cuda.stream(self.d2h):
             for r in batch:
-                r.mate = torch.empty(r.n, dtype=torch.int32, pin_memory=True)
+                if r.mate is None:
+                    r.mate = torch.empty(r.n, dtype=torch.int32, pin_memory=True)
                 r.mate.copy_(r._dev[2], non_blocking=True)
                 r._dev[2].record_stream(self.d2h)
         back = torch.cuda.Event()
         back.record(self.d2h)
         self.ticks += 1
         self.tick_sizes.append(len(batch))
-        return (slot, batch, back)
+        return (slot, batch, back, checked)
 
     def _complete(self, tick) -> bool:
-        slot, batch, back = tick
-        if not back.query():
+        slot, batch, back, checked = tick
+        if not (back.query() and checked.query()):
             return False
         stream, multi = self.slots[slot]
         err = None
@@ -182,7 +197,7 @@ class Server:
             multi.sync(stream)  # the pass's own status (timeouts, bad ids)
         except SkipperError as e:
             err = e
-        verdicts = multi.validate([r._dev for r in batch], stream=stream) if (self.validate and err is None) else None
+        verdicts = multi.verdicts(len(batch)) if (self.validate and err is None) else None
         now = time.perf_counter()
         for i, r in enumerate(batch):
             r.verdict = None if verdicts is None else verdicts[i]

@@ -70,6 +70,9 @@ def test_multi_validate_reports_corruption_per_graph(skp, graphs):
         m.run(tri)
         mates[3][:] = -1                      # graph 3 left unmatched
         verdicts = m.validate(tri)
+        m.validate_async(tri)                 # the enqueued form gives the same verdicts
+        torch.cuda.synchronize()
+        assert [v.as_dict() for v in m.verdicts(len(tri))] == [v.as_dict() for v in verdicts]
         for k, (g, mt, vd) in enumerate(zip(graphs[:6], mates, verdicts)):
             vr = oracle.check(g.offsets.numpy(), g.nbrs.numpy(), _np(mt))
             assert vd.as_dict() == vr.as_dict()
