@@ -342,7 +342,7 @@ def run_batched(args, skp):
 # ----------------------------------------------------------------------------
 # served: Poisson request stream through the continuous-batching server
 # ----------------------------------------------------------------------------
-def run_served(args, skp):
+def run_served(args, skp, min_edges=None, max_edges=None, seconds=None, rate=None):
     import math
     import numpy as np
     import torch
@@ -350,7 +350,11 @@ def run_served(args, skp):
     from paper_2507_04420_gb300.server import Server
     t = time.time()
     P = args.served_pool
-    lo, hi = math.log(args.served_min_edges), math.log(args.served_max_edges)
+    min_edges = args.served_min_edges if min_edges is None else min_edges
+    max_edges = args.served_max_edges if max_edges is None else max_edges
+    seconds = args.served_seconds if seconds is None else seconds
+    rate = args.served_rate if rate is None else rate
+    lo, hi = math.log(min_edges), math.log(max_edges)
     pool = []
     for i in range(P):   # stratified log-uniform sizes, R-MAT and uniform graphs in turn
         m = int(math.exp(lo + (i + 0.5) / P * (hi - lo)))
@@ -363,16 +367,16 @@ def run_served(args, skp):
         del g
     torch.cuda.empty_cache()
     rng = np.random.default_rng(args.seed + 400)
-    gaps = rng.exponential(1.0 / args.served_rate, size=int(args.served_rate * args.served_seconds * 2) + 16)
+    gaps = rng.exponential(1.0 / rate, size=int(rate * seconds * 2) + 16)
     times = np.cumsum(gaps)
-    times = times[times < args.served_seconds]
+    times = times[times < seconds]
     picks = rng.integers(0, P, size=times.size)
     entries = int(sum(pool[p][3] for p in picks))
     log(f"served: pool of {P} graphs ({sum(x[3] for x in pool)} entries) in {time.time() - t:.1f}s; "
-        f"{times.size} requests over {args.served_seconds}s")
-    out = {"workload": f"Poisson arrivals {args.served_rate:g}/s for {args.served_seconds:g}s; each request "
+        f"{times.size} requests over {seconds}s")
+    out = {"workload": f"Poisson arrivals {rate:g}/s for {seconds:g}s; each request "
                        f"one of {P} pre-generated graphs (R-MAT / uniform in turn, undirected edges "
-                       f"log-uniform in [{args.served_min_edges:g}, {args.served_max_edges:g}]) held in "
+                       f"log-uniform in [{min_edges:g}, {max_edges:g}]) held in "
                        "pinned host memory", "requests": int(times.size), "entries": entries}
 
     def run_trace(submit, finish):
@@ -546,6 +550,8 @@ def run_ours(args):
     if not args.no_served:
         torch.cuda.empty_cache()
         served = run_served(args, skp)
+        torch.cuda.empty_cache()
+        served["small_graphs"] = run_served(args, skp, 1e3, 1e5, 1.0, 20000.0)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
