@@ -335,6 +335,30 @@ def complete(n: int, device="cpu") -> CSR:
 # ----------------------------------------------------------------------------
 # batches
 # ----------------------------------------------------------------------------
+def edge_list(g: CSR, order: str = "row", seed: int = 1):
+    """Each undirected edge of a symmetric CSR listed once, as (src, dst) int32 tensors.
+
+    order="row": CSR row order with src < dst (a sorted coordinate list).
+    order="shuffle": the same edges in a seeded random order, each one's
+    direction flipped by a seeded coin (a list in no particular order)."""
+    dev = g.offsets.device
+    deg = g.offsets[1:] - g.offsets[:-1]
+    rows = torch.repeat_interleave(torch.arange(g.n, dtype=torch.int32, device=dev), deg)
+    keep = rows < g.nbrs
+    src, dst = rows[keep], g.nbrs[keep]
+    del rows, keep
+    if order == "row":
+        return src, dst
+    if order != "shuffle":
+        raise ValueError("order must be 'row' or 'shuffle'")
+    m = src.numel()
+    perm = torch.argsort(_draw(seed, 11, 0, m, dev), stable=True)
+    src, dst = src[perm], dst[perm]
+    del perm
+    flip = (_draw(seed, 12, 0, m, dev) & 1).bool()
+    return torch.where(flip, dst, src), torch.where(flip, src, dst)
+
+
 def pack(graphs: Sequence[CSR], device=None) -> Packed:
     """Block-diagonal packing: graph g's vertex x becomes vbase[g] + x."""
     if device is None:

@@ -7,6 +7,9 @@ through ctypes:
   sequential algorithm the paper measures Skipper against, Figs. 9-11).
 * ``check`` -- the exact maximal-matching checker (Section II-B's rule: every
   edge touches an output edge, no two output edges share an endpoint).
+* ``sgmm_edges`` / ``check_edges`` (``edges.c``) -- the same two over a list
+  of edges in coordinate form (Section V-C: Skipper reads such a list
+  directly), SGMM taking the edges in list order.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
 leg may import this package.  It shares no code with the CUDA library under
@@ -29,7 +32,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = [os.path.join(_HERE, "sgmm.c"), os.path.join(_HERE, "check.c")]
+_SOURCES = [os.path.join(_HERE, "sgmm.c"), os.path.join(_HERE, "check.c"),
+            os.path.join(_HERE, "edges.c")]
 _lock = threading.Lock()
 _lib = None
 
@@ -87,6 +91,10 @@ def _load():
             lib.oracle_sgmm_rows_timed.restype = i64
             lib.oracle_check.argtypes = [u64, p, p, p, p, u64, ctypes.POINTER(Verdict)]
             lib.oracle_check.restype = ctypes.c_int
+            lib.oracle_sgmm_edges.argtypes = [u64, u64, p, p, p, p]
+            lib.oracle_sgmm_edges.restype = i64
+            lib.oracle_check_edges.argtypes = [u64, u64, p, p, p, p, u64, ctypes.POINTER(Verdict)]
+            lib.oracle_check_edges.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -168,4 +176,47 @@ def check(offsets, nbrs, mate, pairs=None) -> Verdict:
     rc = _load().oracle_check(n, _ptr(offsets), _ptr(nbrs), _ptr(mate), pp, count, ctypes.byref(v))
     if rc != 0:
         raise MemoryError("oracle_check: no memory")
+    return v
+
+
+def _edges(n, src, dst):
+    src, dst = _u32(src), _u32(dst)
+    if src.ndim != 1 or src.shape != dst.shape:
+        raise ValueError("src and dst must be 1-D arrays of the same length")
+    return int(n), src, dst
+
+
+def sgmm_edges(n, src, dst):
+    """SGMM over the edge list (src[i], dst[i]) in list order.
+
+    Returns (mate uint32[n], pairs uint32[k, 2]) with pairs in the order taken."""
+    n, src, dst = _edges(n, src, dst)
+    mate = np.empty(n, dtype=np.uint32)
+    pairs = np.empty((max(n // 2, 1), 2), dtype=np.uint32)
+    k = _load().oracle_sgmm_edges(n, src.size, _ptr(src), _ptr(dst), _ptr(mate), _ptr(pairs))
+    if k < 0:
+        raise ValueError("oracle_sgmm_edges failed (endpoint id out of range or no memory)")
+    return mate, pairs[:k].copy()
+
+
+def check_edges(n, src, dst, mate, pairs=None) -> Verdict:
+    """Exact checker with the edge list as the edge set; first_uncovered is an
+    index into the list."""
+    n, src, dst = _edges(n, src, dst)
+    mate = _u32(mate)
+    if mate.size != n:
+        raise ValueError("mate must have n entries")
+    count = 0
+    pp = None
+    if pairs is not None:
+        pairs = _u32(pairs).reshape(-1, 2)
+        count = pairs.shape[0]
+        if count == 0:
+            pairs = np.zeros((1, 2), dtype=np.uint32)
+        pp = _ptr(pairs)
+    v = Verdict()
+    rc = _load().oracle_check_edges(n, src.size, _ptr(src), _ptr(dst), _ptr(mate), pp, count,
+                                    ctypes.byref(v))
+    if rc != 0:
+        raise MemoryError("oracle_check_edges: no memory")
     return v
