@@ -192,6 +192,28 @@ mm_status mm_create_csr(uint64_t n, uint64_t nnz, const int64_t *d_offsets,
                         mm_graph **out);
 
 /*
+ * Create a handle over an edge list in coordinate form (Section V-C: Skipper
+ * may read its input as a list of edges, with no symmetrisation).  Edge i is
+ * {d_src[i], d_dst[i]}; each undirected edge needs to be listed once, in
+ * either direction, in any order; repeats and self-loops are allowed (a
+ * repeat is resolved at once by the line-10 test, a loop is skipped).
+ *   d_src, d_dst  uint32_t[m] in device memory, borrowed, 4-byte aligned
+ *                 (16-byte aligned for 128-bit loads; otherwise 32-bit loads).
+ * The handle owns its state array and control words, as for a CSR.  With
+ * MM_CHECK_CSR every id is checked (< n) on the device before returning.
+ * mm_skipper on this handle runs Algorithm 1 for every listed edge (there is
+ * no row, so none is skipped; o->grain counts edges per work unit); serial
+ * mode takes the edges in list order and equals sequential greedy over the
+ * list.  mm_validate checks against the listed edges (first_uncovered is a
+ * list index); mm_get_stats counts 128-edge tiles as chunks.  The batched
+ * calls reject this handle with MM_ERR_UNSUPPORTED.
+ * Errors: MM_ERR_ARG (null out, n > MM_MAX_VERTICES, null arrays with m > 0,
+ * misaligned arrays, unknown flags), MM_ERR_OOM, MM_ERR_CUDA, MM_ERR_BAD_GRAPH.
+ */
+mm_status mm_create_coo(uint64_t n, uint64_t m, const uint32_t *d_src, const uint32_t *d_dst,
+                        uint32_t flags, void *cuda_stream, mm_graph **out);
+
+/*
  * Skipper's single pass (Algorithm 1): every vertex starts ACC (lines 3-4);
  * every stored entry (x, y), x != y, is resolved once with u = min(x, y),
  * v = max(x, y): reserve u ACC->RSVD, claim v ACC->MCHD, then set u MCHD or

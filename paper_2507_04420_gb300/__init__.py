@@ -20,7 +20,7 @@ import torch
 from . import _native
 from ._native import GraphDesc, Options, Stats, Timing, Verdict
 
-__all__ = ["Graph", "HostSession", "Multi", "SkipperError", "match", "validate", "Options", "Verdict", "Timing",
+__all__ = ["EdgeList", "Graph", "HostSession", "Multi", "SkipperError", "match", "validate", "Options", "Verdict", "Timing",
            "UNMATCHED", "lib", "options"]
 
 UNMATCHED = 0xFFFFFFFF
@@ -84,6 +84,7 @@ class Graph:
         _need(offsets, "offsets", (torch.int64,))
         _need(nbrs, "nbrs", _U32)
         self.offsets, self.nbrs = offsets, nbrs
+        self.device = offsets.device
         self.n = offsets.numel() - 1
         self.nnz = nbrs.numel()
         h = ctypes.c_void_p()
@@ -97,7 +98,7 @@ class Graph:
                 cap: Optional[int] = None, stream=None, opts: Optional[Options] = None, **kw):
         """Run Skipper; returns mate (int32 view of uint32), plus (pairs, count) if asked."""
         o = opts if opts is not None else options(**kw)
-        dev = self.offsets.device
+        dev = self.device
         if mate is None:
             mate = torch.empty(self.n, dtype=torch.int32, device=dev)
         _need(mate, "mate", _U32)
@@ -123,9 +124,9 @@ class Graph:
         o = opts if opts is not None else options(**kw)
         G = vbase.numel() - 1
         if mate is None:
-            mate = torch.empty(self.n, dtype=torch.int32, device=self.offsets.device)
+            mate = torch.empty(self.n, dtype=torch.int32, device=self.device)
         _need(mate, "mate", _U32)
-        gp = torch.empty(G, dtype=torch.int64, device=self.offsets.device) if graph_pairs else None
+        gp = torch.empty(G, dtype=torch.int64, device=self.device) if graph_pairs else None
         _check(lib.mm_skipper_batched(self._h, G, _ptr(vbase), _ptr(ebase), ctypes.byref(o),
                                       _ptr(mate), _ptr(gp), _stream_ptr(stream)),
                "mm_skipper_batched")
@@ -134,7 +135,7 @@ class Graph:
     def autotune_batched(self, vbase: torch.Tensor, ebase: torch.Tensor, stream=None,
                          opts: Optional[Options] = None, **kw) -> Options:
         o = opts if opts is not None else options(**kw)
-        scratch = torch.empty(self.n, dtype=torch.int32, device=self.offsets.device)
+        scratch = torch.empty(self.n, dtype=torch.int32, device=self.device)
         _check(lib.mm_autotune_batched(self._h, vbase.numel() - 1, _ptr(vbase), _ptr(ebase),
                                        _ptr(scratch), ctypes.byref(o), _stream_ptr(stream)),
                "mm_autotune_batched")
@@ -195,6 +196,28 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+class EdgeList(Graph):
+    """A device edge-list handle (mm_create_coo): edge i is {src[i], dst[i]},
+    each edge listed once in either direction.  Borrows src/dst, which must
+    outlive it.  skipper / validate / stats / timing work as on a CSR handle;
+    the batched calls do not apply."""
+
+    def __init__(self, n: int, src: torch.Tensor, dst: torch.Tensor, check: bool = True, stream=None):
+        _need(src, "src", _U32)
+        _need(dst, "dst", _U32)
+        if src.dim() != 1 or src.shape != dst.shape:
+            raise ValueError("src and dst must be 1-D tensors of the same length")
+        self.src, self.dst = src, dst
+        self.device = src.device
+        self.n = int(n)
+        self.nnz = self.m = src.numel()
+        h = ctypes.c_void_p()
+        _check(lib.mm_create_coo(self.n, self.m, _ptr(src) if self.m else None,
+                                 _ptr(dst) if self.m else None, 1 if check else 0,
+                                 _stream_ptr(stream), ctypes.byref(h)), "mm_create_coo")
+        self._h = h
 
 
 def match(offsets: torch.Tensor, nbrs: torch.Tensor, **kw) -> torch.Tensor:

@@ -19,7 +19,7 @@ CSRC = os.path.join(_PKG, "csrc")
 INCLUDE = os.path.join(_ROOT, "include")
 LIB_DIR = os.path.join(_PKG, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libskipper.so")
-SOURCES = ["sweep.cu", "check.cu", "api.cu", "noalloc.cu", "multi.cu"]
+SOURCES = ["sweep.cu", "check.cu", "api.cu", "noalloc.cu", "multi.cu", "coo.cu"]
 HEADERS = ["state.cuh", "internal.h", "walk.cuh", "checkwalk.cuh"]
 
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -158,6 +158,7 @@ SYMBOLS = [
     ("mm_last_error", ctypes.c_char_p, []),
     ("mm_default_options", _I, [ctypes.POINTER(Options)]),
     ("mm_create_csr", _I, [_U64, _U64, _P, _P, _U32, _P, ctypes.POINTER(_P)]),
+    ("mm_create_coo", _I, [_U64, _U64, _P, _P, _U32, _P, ctypes.POINTER(_P)]),
     ("mm_skipper", _I, [_P, ctypes.POINTER(Options), _P, _P, _U64, _P, _P]),
     ("mm_skipper_batched", _I, [_P, _U64, _P, _P, ctypes.POINTER(Options), _P, _P, _P]),
     ("mm_validate", _I, [_P, _P, _P, _U64, ctypes.POINTER(Verdict), _P]),

@@ -63,9 +63,12 @@ void skp::set_error_message(const char* fmt, ...) {
 struct mm_graph {
   int device = 0;
   int num_sms = 0;
-  uint64_t n = 0, nnz = 0;
+  uint64_t n = 0, nnz = 0;            // nnz: stored entries (CSR) or listed edges (edge list)
+  bool coo = false;                   // made by mm_create_coo: an edge list, no CSR
   const int64_t* offsets = nullptr;
   const uint32_t* nbrs = nullptr;
+  const uint32_t* src = nullptr;      // edge list (coo): edge i = (src[i], dst[i])
+  const uint32_t* dst = nullptr;
   uint32_t* state = nullptr;          // ceil(n/4) words (+ slack)
   int64_t* part = nullptr;
   uint64_t part_units_cap = 0;
@@ -264,6 +267,58 @@ mm_status check_handle(const mm_graph* g) {
   return MM_OK;
 }
 
+// mm_skipper on an edge-list handle: prepare, the edge-list sweep (or its
+// serial form), the optional ordered pair list, the status read.
+mm_status skipper_coo(mm_graph* g, const Resolved& r, uint32_t* d_mate, uint32_t* d_pairs,
+                      uint64_t cap, uint64_t* d_count, cudaStream_t s) {
+  mm_status st = MM_OK;
+  CooParams C{};
+  C.P.n = g->n;
+  C.P.nnz = g->nnz;
+  C.P.mate = d_mate;
+  C.P.state = r.word ? d_mate : g->state;
+  C.P.work = work_ptr(g);
+  C.P.err = err_ptr(g);
+  C.P.spin_limit = r.spin_limit;
+  C.P.poison = r.poison;
+  C.src = g->src;
+  C.dst = g->dst;
+  C.m = g->nnz;
+  C.grain = r.grain;
+  C.units = (g->nnz + r.grain - 1) / r.grain;
+  C.vec = ((reinterpret_cast<uintptr_t>(g->src) | reinterpret_cast<uintptr_t>(g->dst)) & 15u) == 0;
+  g->stats_valid = false;
+  if (r.stats && !r.serial) {
+    if (!g->stats) CUDA_TRY(cudaMalloc(&g->stats, kStCount * sizeof(unsigned long long)));
+    C.P.stats = g->stats;
+    g->stats_valid = true;
+  }
+  CheckScratch cs{counters_ptr(g), g->seen_bits, g->tile_counts, g->tile_cap, nullptr, nullptr};
+  cudaEvent_t* ev = nullptr;
+  if (r.timing) {
+    if ((st = ensure_hist(g)) != MM_OK) return st;
+    ev = next_hist(g, C.units, d_pairs || d_count);
+    CUDA_TRY(cudaEventRecord(ev[0], s));
+  }
+  CUDA_TRY(launch_coo_prepare(C, r.bits, prepare_grid(g), s));
+  if (ev) CUDA_TRY(cudaEventRecord(ev[1], s));
+  L2Window win;
+  if (!r.serial) {
+    const int per_sm = r.blocks_per_sm > 0 ? r.blocks_per_sm : coo_blocks_per_sm(r.bits, r.block);
+    if ((st = win.open(g, r, s, C.P.state, r.word ? g->n * 4 : packed_words(g->n, r.bits) * 4)) != MM_OK) return st;
+    CUDA_TRY(launch_coo_sweep(C, r.bits, g->num_sms * per_sm, r.block, s));
+    if ((st = win.close()) != MM_OK) return st;
+  } else {
+    CUDA_TRY(launch_coo_serial(C, r.bits, s));
+  }
+  if (ev) CUDA_TRY(cudaEventRecord(ev[2], s));
+  if (d_pairs || d_count) CUDA_TRY(launch_compact(g->n, d_mate, d_pairs, d_pairs ? cap : 0, d_count, cs, s));
+  if (ev) CUDA_TRY(cudaEventRecord(ev[3], s));
+  CUDA_TRY(cudaMemcpyAsync(g->h_err, err_ptr(g), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  if (r.nosync) return MM_OK;
+  return read_err(g, s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -279,6 +334,65 @@ mm_status mm_default_options(mm_options* o) {
   o->grain = kDefaultGrain;
   o->block_threads = kDefaultBlock;
   o->spin_limit = kDefaultSpin;
+  return MM_OK;
+}
+
+mm_status mm_create_coo(uint64_t n, uint64_t m, const uint32_t* d_src, const uint32_t* d_dst,
+                        uint32_t flags, void* cuda_stream, mm_graph** out) {
+  g_err[0] = 0;
+  if (!out) return fail(MM_ERR_ARG, "null out");
+  *out = nullptr;
+  if (n > MM_MAX_VERTICES) return fail(MM_ERR_ARG, "n = %llu exceeds %llu", (unsigned long long)n, MM_MAX_VERTICES);
+  if (m && (!d_src || !d_dst)) return fail(MM_ERR_ARG, "null src / dst with m > 0");
+  if ((reinterpret_cast<uintptr_t>(d_src) | reinterpret_cast<uintptr_t>(d_dst)) & 3u)
+    return fail(MM_ERR_ARG, "src and dst must be 4-byte aligned");
+  if (flags & ~MM_CHECK_CSR) return fail(MM_ERR_ARG, "unknown flags 0x%x", flags);
+  int ndev = 0;
+  CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (ndev <= 0) return fail(MM_ERR_CUDA, "no CUDA device");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+
+  mm_graph* g = new (std::nothrow) mm_graph();
+  if (!g) return fail(MM_ERR_OOM, "host allocation failed");
+  auto bail = [&](mm_status code) {
+    mm_destroy(g);
+    return code;
+  };
+#define CREATE_TRY(expr)                                                                   \
+  do {                                                                                     \
+    cudaError_t e_ = (expr);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return bail(fail(e_ == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA, "%s: %s", \
+                       #expr, cudaGetErrorString(e_)));                                    \
+  } while (0)
+  CREATE_TRY(cudaGetDevice(&g->device));
+  CREATE_TRY(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device));
+  g->coo = true;
+  g->n = n;
+  g->nnz = m;
+  g->src = d_src;
+  g->dst = d_dst;
+  const uint64_t words = (n + 3) / 4 + 4;
+  CREATE_TRY(cudaMalloc(&g->state, words * sizeof(uint32_t)));
+  CREATE_TRY(cudaMalloc(&g->ctrl, 32 * sizeof(unsigned long long)));
+  CREATE_TRY(cudaMemsetAsync(g->ctrl, 0, 32 * sizeof(unsigned long long), s));
+  g->tile_cap = (n + kCompactTile - 1) / kCompactTile + 1;
+  CREATE_TRY(cudaMalloc(&g->tile_counts, g->tile_cap * sizeof(uint64_t)));
+  CREATE_TRY(cudaMallocHost(&g->h_err, 64));
+  CREATE_TRY(cudaMallocHost(&g->h_counters, 16 * sizeof(unsigned long long)));
+  *g->h_err = 0;
+  for (auto& e : g->ev) CREATE_TRY(cudaEventCreate(&e));
+  if (flags & MM_CHECK_CSR) {
+    CREATE_TRY(launch_coo_check(n, m, d_src, d_dst, csr_bad_ptr(g), prepare_grid(g), s));
+    CREATE_TRY(cudaMemcpyAsync(g->h_counters, csr_bad_ptr(g), sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, s));
+    CREATE_TRY(cudaStreamSynchronize(s));
+    if (g->h_counters[0] != 0)
+      return bail(fail(MM_ERR_BAD_GRAPH, "edge-list check failed: %llu endpoint ids >= n",
+                       g->h_counters[0]));
+  }
+#undef CREATE_TRY
+  *out = g;
   return MM_OK;
 }
 
@@ -356,6 +470,7 @@ mm_status mm_skipper(mm_graph* g, const mm_options* o, uint32_t* d_mate, uint32_
   Resolved r;
   if ((st = resolve(g, o, &r)) != MM_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (g->coo) return skipper_coo(g, r, d_mate, d_pairs, cap, d_count, s);
   const uint64_t units = (g->n + g->nnz + r.grain - 1) / r.grain;
   if ((st = ensure_part(g, units)) != MM_OK) return st;
   SweepParams P = make_params(g, r, d_mate);
@@ -543,6 +658,7 @@ mm_status mm_skipper_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d_
   g_err[0] = 0;
   mm_status st = check_handle(g);
   if (st != MM_OK) return st;
+  if (g->coo) return fail(MM_ERR_UNSUPPORTED, "batched calls take a CSR handle");
   if (num_graphs == 0) return fail(MM_ERR_ARG, "num_graphs = 0");
   if (!d_vbase || !d_ebase) return fail(MM_ERR_ARG, "null vbase / ebase");
   if (!d_mate && g->n) return fail(MM_ERR_ARG, "null mate");
@@ -606,11 +722,17 @@ mm_status mm_validate(mm_graph* g, const uint32_t* d_mate, const uint32_t* d_pai
     CUDA_TRY(cudaMalloc(&g->seen_bits, ((g->n + 31) / 32 + 1) * sizeof(uint32_t)));
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   if (!g->found) CUDA_TRY(cudaMalloc(&g->found, g->n + 16));
-  if (!g->check_part)
-    CUDA_TRY(cudaMalloc(&g->check_part, ((g->n + g->nnz) / kCheckGrain + 2) * 2 * sizeof(int64_t)));
-  CheckScratch cs{counters_ptr(g), g->seen_bits, g->tile_counts, g->tile_cap, g->found, g->check_part};
-  CUDA_TRY(launch_validate(g->n, g->nnz, g->offsets, g->nbrs, d_mate, d_pairs, d_pairs ? count : 0, cs,
-                           prepare_grid(g), s));
+  if (g->coo) {
+    CheckScratch cs{counters_ptr(g), g->seen_bits, g->tile_counts, g->tile_cap, g->found, nullptr};
+    CUDA_TRY(launch_validate_coo(g->n, g->nnz, g->src, g->dst, d_mate, d_pairs, d_pairs ? count : 0, cs,
+                                 prepare_grid(g), s));
+  } else {
+    if (!g->check_part)
+      CUDA_TRY(cudaMalloc(&g->check_part, ((g->n + g->nnz) / kCheckGrain + 2) * 2 * sizeof(int64_t)));
+    CheckScratch cs{counters_ptr(g), g->seen_bits, g->tile_counts, g->tile_cap, g->found, g->check_part};
+    CUDA_TRY(launch_validate(g->n, g->nnz, g->offsets, g->nbrs, d_mate, d_pairs, d_pairs ? count : 0, cs,
+                             prepare_grid(g), s));
+  }
   CUDA_TRY(cudaMemcpyAsync(g->h_counters, counters_ptr(g), 9 * sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -641,6 +763,7 @@ mm_status mm_autotune_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d
   mm_status st = check_handle(g);
   if (st != MM_OK) return st;
   if (!o || !d_mate_scratch) return fail(MM_ERR_ARG, "null options or scratch");
+  if (g->coo) return fail(MM_ERR_UNSUPPORTED, "batched calls take a CSR handle");
   static const uint32_t grains[] = {1024, 2048, 4096, 8192};
   static const uint32_t bits[] = {2, 8, 32};
   static const uint32_t blocks[] = {256, 512};

@@ -46,6 +46,16 @@ __global__ void csr_check_kernel(uint64_t n, uint64_t nnz, const int64_t* __rest
   if (local) atomicAdd(bad, local);
 }
 
+// edge-list input: every endpoint id < n
+__global__ void coo_check_kernel(uint64_t n, uint64_t m, const uint32_t* __restrict__ src,
+                                 const uint32_t* __restrict__ dst, unsigned long long* bad) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  unsigned long long local = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride)
+    local += (src[i] >= n) + (dst[i] >= n);
+  if (local) atomicAdd(bad, local);
+}
+
 __device__ __forceinline__ void warp_add(unsigned long long* c, uint32_t v) {
   const uint32_t s = __reduce_add_sync(kFull, v);
   if ((threadIdx.x & 31) == 0 && s) atomicAdd(c, (unsigned long long)s);
@@ -81,6 +91,40 @@ __global__ void validate_edges_kernel(uint64_t n, uint64_t nnz, const int64_t* _
   for (uint64_t u = warp; u < units; u += nwarps) {
     const int64_t e0 = part[2 * u + 1], e1 = part[2 * u + 3];
     if (e0 < e1) check_unit(offsets, nbrs, n, nnz, mate, found, part[2 * u], e0, e1, lane, unc, first);
+  }
+  unc = warp_sum64(unc);
+  first = warp_min64(first);
+  if (lane == 0) {
+    if (unc) atomicAdd(c + C_UNCOVERED, unc);
+    if (first != ~0ull) atomicMin(c + C_FIRST_UNCOVERED, first);
+  }
+}
+
+// edge pass over an edge list: edge i = (x, y), x != y, both ids < n, is
+// uncovered when both endpoints are unmatched; mate[x] == y marks found[x] and
+// mate[y] == x marks found[y] (the listed edge is the output edge of x / y)
+__global__ void validate_coo_edges_kernel(uint64_t n, uint64_t m, const uint32_t* __restrict__ src,
+                                          const uint32_t* __restrict__ dst,
+                                          const uint32_t* __restrict__ mate,
+                                          unsigned char* __restrict__ found,
+                                          unsigned long long* __restrict__ c) {
+  const unsigned lane = threadIdx.x & 31u;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  unsigned long long unc = 0, first = ~0ull;
+  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < m; i0 += stride) {
+    const uint64_t i = i0 + threadIdx.x;
+    if (i < m) {
+      const uint32_t x = __ldg(src + i), y = __ldg(dst + i);
+      if (x != y && x < n && y < n) {
+        const uint32_t mx = __ldg(mate + x), my = __ldg(mate + y);
+        if (mx == kNone && my == kNone) {
+          ++unc;
+          if (i < first) first = i;
+        }
+        if (mx == y) found[x] = 1;
+        if (my == x) found[y] = 1;
+      }
+    }
   }
   unc = warp_sum64(unc);
   first = warp_min64(first);
@@ -273,6 +317,28 @@ cudaError_t launch_validate(uint64_t n, uint64_t nnz, const int64_t* offsets, co
     const uint64_t units = (n + nnz + kCheckGrain - 1) / kCheckGrain;
     check_partition_kernel<<<grid, 256, 0, s>>>(n, nnz, offsets, kCheckGrain, units, cs.part);
     if (nnz) validate_edges_kernel<<<grid, 256, 0, s>>>(n, nnz, offsets, nbrs, mate, cs.found, cs.part, units, cs.counters);
+    validate_vertex_kernel<<<grid, 256, 0, s>>>(n, mate, cs.found, cs.counters);
+  }
+  if (pairs && count) validate_pairs_kernel<<<grid, 256, 0, s>>>(n, mate, pairs, count, cs.seen_bits, cs.counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coo_check(uint64_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
+                             unsigned long long* bad, int grid, cudaStream_t s) {
+  zero_u64_kernel<<<1, 32, 0, s>>>(bad, 1, 0ull);
+  if (m) coo_check_kernel<<<grid, 256, 0, s>>>(n, m, src, dst, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate_coo(uint64_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
+                                const uint32_t* mate, const uint32_t* pairs, uint64_t count,
+                                const CheckScratch& cs, int grid, cudaStream_t s) {
+  zero_u64_kernel<<<1, 32, 0, s>>>(cs.counters, C_FIRST_BAD, 0ull);
+  zero_u64_kernel<<<1, 32, 0, s>>>(cs.counters + C_FIRST_BAD, 2, ~0ull);
+  if (pairs && count) zero_u32_kernel<<<grid, 256, 0, s>>>(cs.seen_bits, (n + 31) / 32);
+  if (n) {
+    zero_u32_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<uint32_t*>(cs.found), (n + 3) / 4);
+    if (m) validate_coo_edges_kernel<<<grid, 256, 0, s>>>(n, m, src, dst, mate, cs.found, cs.counters);
     validate_vertex_kernel<<<grid, 256, 0, s>>>(n, mate, cs.found, cs.counters);
   }
   if (pairs && count) validate_pairs_kernel<<<grid, 256, 0, s>>>(n, mate, pairs, count, cs.seen_bits, cs.counters);

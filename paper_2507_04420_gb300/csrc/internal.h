@@ -19,6 +19,21 @@ void get_batched_kernels(int bits, bool serial, const void** prepare, const void
 cudaError_t launch_graph_pairs(const uint32_t* mate, const int64_t* vbase, uint64_t num_graphs,
                                uint64_t n, uint64_t* graph_pairs, int grid, cudaStream_t s);
 
+// coo.cu: Skipper over an edge list (src[i], dst[i]) in coordinate form
+struct CooParams {
+  SweepParams P;        // n, state, mate, work, err, spin_limit, poison, stats (CSR fields unused)
+  const uint32_t* src;  // m endpoint ids
+  const uint32_t* dst;  // m endpoint ids
+  uint64_t m;           // listed edges
+  uint64_t units;       // ceil(m / grain)
+  uint32_t grain;       // edges per work unit, a multiple of 128
+  uint32_t vec;         // 1 when src and dst are 16-byte aligned (128-bit loads)
+};
+int coo_blocks_per_sm(int bits, int block_threads);
+cudaError_t launch_coo_prepare(const CooParams& C, int bits, int grid, cudaStream_t s);
+cudaError_t launch_coo_sweep(const CooParams& C, int bits, int grid, int block, cudaStream_t s);
+cudaError_t launch_coo_serial(const CooParams& C, int bits, cudaStream_t s);
+
 // api.cu: message returned by mm_last_error() on this thread
 void set_error_message(const char* fmt, ...);
 
@@ -38,6 +53,11 @@ cudaError_t launch_csr_check(uint64_t n, uint64_t nnz, const int64_t* offsets,
 cudaError_t launch_validate(uint64_t n, uint64_t nnz, const int64_t* offsets, const uint32_t* nbrs,
                             const uint32_t* mate, const uint32_t* pairs, uint64_t count,
                             const CheckScratch& cs, int grid, cudaStream_t s);
+cudaError_t launch_coo_check(uint64_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
+                             unsigned long long* bad, int grid, cudaStream_t s);
+cudaError_t launch_validate_coo(uint64_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
+                                const uint32_t* mate, const uint32_t* pairs, uint64_t count,
+                                const CheckScratch& cs, int grid, cudaStream_t s);
 constexpr uint64_t kCompactTile = 4096;  // vertices per compaction tile
 cudaError_t launch_compact(uint64_t n, const uint32_t* mate, uint32_t* pairs, uint64_t cap,
                            uint64_t* count, const CheckScratch& cs, cudaStream_t s);
