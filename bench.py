@@ -235,6 +235,23 @@ def cpu_sample(off_np, nb_np, seconds):
 # ----------------------------------------------------------------------------
 # reference arm: the oracle on the host cores
 # ----------------------------------------------------------------------------
+def skipper_cpu_sample(off_np, nb_np, threads, row_skip, seconds):
+    """Algorithm 1 on host threads over rows [0, R), R sized to about `seconds`,
+    with SGMM timed over the same rows."""
+    import numpy as np
+    import oracle
+    n = off_np.size - 1
+    r = int(min(n, max(4096, n // 256)))
+    _, sec, _ = oracle.cpu_skipper(off_np, nb_np, threads, row_skip, rows=(0, r))
+    rate = int(off_np[r]) / max(sec, 1e-6)
+    R = int(min(n, max(r, np.searchsorted(off_np, rate * seconds))))
+    _, sec, cnf = oracle.cpu_skipper(off_np, nb_np, threads, row_skip, rows=(0, R))
+    _, sgmm_sec, ent = oracle.sgmm_rows_timed(off_np, nb_np, R)
+    return {"threads": threads, "row_skip": bool(row_skip), "rows": R, "entries": ent,
+            "seconds": sec, "gedges_s": ent / sec / 1e9, "failed_cas": cnf,
+            "sgmm_seconds_same_rows": sgmm_sec}
+
+
 def run_reference(args):
     import numpy as np
     world, rank, _ = dist_env()
@@ -608,6 +625,52 @@ def run_ours(args):
                          f"{cs['entries']} entries ({100.0 * cs['entries'] / nnz:.1f}% of nnz) "
                          f"in {cs['seconds']:.2f}s"}
 
+    cpu_skipper = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the paper's own setting on this host (Section VI-D): Algorithm 1 on all
+        # host cores (as printed, and with the row skip) and on one core, each
+        # against SGMM over the same rows
+        T = os.cpu_count() or 1
+        par = skipper_cpu_sample(off_np, nb_np, T, False, args.cpu_seconds / 4)
+        par_rs = skipper_cpu_sample(off_np, nb_np, T, True, args.cpu_seconds / 4)
+        one = skipper_cpu_sample(off_np, nb_np, 1, False, args.cpu_seconds / 8)
+        one_rs = skipper_cpu_sample(off_np, nb_np, 1, True, args.cpu_seconds / 8)
+        cpu_skipper = {
+            "kind": "Algorithm 1 on host threads (oracle/skipper_cpu.c), not the oracle",
+            "host_cores": T,
+            "parallel": par, "parallel_row_skip": par_rs, "one_thread": one, "one_thread_row_skip": one_rs,
+            "parallelization_gain": par["sgmm_seconds_same_rows"] / par["seconds"],
+            "parallelization_gain_row_skip": par_rs["sgmm_seconds_same_rows"] / par_rs["seconds"],
+            "serial_slowdown": one["seconds"] / one["sgmm_seconds_same_rows"],
+            "serial_slowdown_row_skip": one_rs["seconds"] / one_rs["sgmm_seconds_same_rows"],
+            "gpu_vs_host_skipper": value / max(par["gedges_s"], par_rs["gedges_s"]),
+            "how": "parallelization gain = t_SGMM / t_Skipper(T threads), serial slowdown = "
+                   "t_Skipper(1 thread) / t_SGMM (Section VI-D, Figs. 10-11), each pair on the "
+                   "same rows [0, R) of this graph, R sized by a short calibration",
+        }
+
+    serial_mode = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # one GPU thread walking the CSR in SGMM order (serial mode) against SGMM
+        # on one host core, on the ER graph of n = 100,000, m = 1,000,000
+        import oracle
+        import graphgen as gg
+        er = gg.erdos_renyi(100_000, 1_000_000, seed=args.seed)
+        er_d = er.to("cuda")
+        with skp.Graph(er_d.offsets, er_d.nbrs) as he:
+            he.skipper(serial=1, status_bits=8)
+            ts = []
+            for _ in range(3):
+                he.skipper(serial=1, status_bits=8, timing=1)
+                ts.append(he.timing()["total_ms"])
+        _, sgmm_s = oracle.sgmm_timed(er.offsets.numpy(), er.nbrs.numpy())
+        serial_mode = {"workload": "erdos_renyi n=100000 m=1000000 (nnz 2000000)",
+                       "gpu_one_thread_ms": statistics.median(ts), "sgmm_one_core_ms": sgmm_s * 1e3,
+                       "ratio": statistics.median(ts) / (sgmm_s * 1e3),
+                       "how": "mm_skipper serial=1 (one GPU thread, CUDA events) vs the oracle's SGMM "
+                              "(one host core); a GPU thread is not a CPU core: this is the cost of the "
+                              "debug mode, not a kernel-quality figure"}
+
     batched = None
     h.close()
     del g, h_off, h_nb
@@ -645,6 +708,8 @@ def run_ours(args):
         "batched": batched,
         "served": served,
         "cpu_baseline": cpu,
+        "cpu_skipper": cpu_skipper,
+        "serial_mode": serial_mode,
         "e2e": e2e,
         "gpu_launches": 2 * args.steps,
         "clocks": clk,

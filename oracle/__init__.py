@@ -7,6 +7,10 @@ through ctypes:
   sequential algorithm the paper measures Skipper against, Figs. 9-11).
 * ``check`` -- the exact maximal-matching checker (Section II-B's rule: every
   edge touches an output edge, no two output edges share an endpoint).
+* ``cpu_skipper`` (``skipper_cpu.c``) -- not an oracle: Algorithm 1 on host
+  threads, the paper's own setting, a CPU baseline for the benchmark
+  (parallelization gain and serial slowdown, Section VI-D); its results are
+  checked with ``check``.
 * ``sgmm_edges`` / ``check_edges`` (``edges.c``) -- the same two over a list
   of edges in coordinate form (Section V-C: Skipper reads such a list
   directly), SGMM taking the edges in list order.
@@ -33,7 +37,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _SOURCES = [os.path.join(_HERE, "sgmm.c"), os.path.join(_HERE, "check.c"),
-            os.path.join(_HERE, "edges.c")]
+            os.path.join(_HERE, "edges.c"), os.path.join(_HERE, "skipper_cpu.c")]
 _lock = threading.Lock()
 _lib = None
 
@@ -70,8 +74,8 @@ def build(force: bool = False) -> str:
     newest = max(os.path.getmtime(s) for s in _SOURCES)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-D_POSIX_C_SOURCE=199309L", "-shared",
-                               "-fPIC", "-o", tmp, *_SOURCES])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-D_POSIX_C_SOURCE=200809L", "-pthread",
+                               "-shared", "-fPIC", "-o", tmp, *_SOURCES])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -91,6 +95,9 @@ def _load():
             lib.oracle_sgmm_rows_timed.restype = i64
             lib.oracle_check.argtypes = [u64, p, p, p, p, u64, ctypes.POINTER(Verdict)]
             lib.oracle_check.restype = ctypes.c_int
+            lib.cpu_skipper.argtypes = [u64, p, p, u64, u64, ctypes.c_int, u64, ctypes.c_int, p,
+                                        ctypes.POINTER(ctypes.c_double)]
+            lib.cpu_skipper.restype = i64
             lib.oracle_sgmm_edges.argtypes = [u64, u64, p, p, p, p]
             lib.oracle_sgmm_edges.restype = i64
             lib.oracle_check_edges.argtypes = [u64, u64, p, p, p, p, u64, ctypes.POINTER(Verdict)]
@@ -220,3 +227,23 @@ def check_edges(n, src, dst, mate, pairs=None) -> Verdict:
     if rc != 0:
         raise MemoryError("oracle_check_edges: no memory")
     return v
+
+
+def cpu_skipper(offsets, nbrs, threads: int, row_skip: bool = False, rows=None,
+                block_edges: int = 1 << 16):
+    """Algorithm 1 on `threads` host threads over rows [r0, r1) (default: all).
+
+    Returns (mate uint32[n], seconds of the parallel pass, failed CAS count)."""
+    offsets = np.ascontiguousarray(np.asarray(offsets), dtype=np.int64)
+    nbrs = _u32(nbrs)
+    n = offsets.size - 1
+    r0, r1 = (0, n) if rows is None else (int(rows[0]), int(min(rows[1], n)))
+    mate = np.empty(n, dtype=np.uint32)
+    sec = ctypes.c_double(0.0)
+    rc = _load().cpu_skipper(n, _ptr(offsets), _ptr(nbrs), r0, r1, int(threads), int(block_edges),
+                             1 if row_skip else 0, _ptr(mate), ctypes.byref(sec))
+    if rc == -2:
+        raise RuntimeError("cpu_skipper: a wait ran past its bound")
+    if rc < 0:
+        raise RuntimeError("cpu_skipper: allocation or thread start failed")
+    return mate, float(sec.value), int(rc)
