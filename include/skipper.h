@@ -98,7 +98,17 @@ typedef struct mm_options {
     uint64_t poison_vertex;  /* fault injection for tests: v + 1 leaves vertex v
                                 RESERVED by no thread after initialisation, so
                                 every wait on it runs out; 0 = off */
-    uint64_t reserved[4];
+    uint32_t symmetric;      /* 1: the caller asserts that the CSR is symmetric (every
+                                edge stored in the rows of both endpoints).  The
+                                parallel sweep then tests each edge once, from the
+                                row of its lower endpoint, and leaves entries (x, y)
+                                with y < x to row y (Section V-C: one pass over the
+                                edges needs each edge once); this halves the state
+                                reads.  On a CSR that is not symmetric the result
+                                is in general not maximal.  Serial mode and the
+                                edge-list and multi-graph calls ignore it.  0 = off. */
+    uint32_t reserved32;
+    uint64_t reserved[3];
 } mm_options;
 
 /* Per-kernel device times of the last call made with options.timing = 1. */

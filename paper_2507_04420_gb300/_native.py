@@ -86,7 +86,9 @@ class Options(ctypes.Structure):
         ("stats", ctypes.c_uint32),
         ("spin_limit", ctypes.c_uint64),
         ("poison_vertex", ctypes.c_uint64),
-        ("reserved", ctypes.c_uint64 * 4),
+        ("symmetric", ctypes.c_uint32),
+        ("reserved32", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint64 * 3),
     ]
 
 

@@ -47,6 +47,7 @@ struct BatchGraph {
   cudaGraphNode_t n_prepare = nullptr, n_sweep = nullptr, n_pairs = nullptr, n_copy = nullptr;
   // signature of the options the graph was built for
   uint32_t status_bits = 0, serial = 0, grain = 0, block = 0, blocks_per_sm = 0;
+  bool sym = false;
   bool with_pairs = false;
   uint64_t num_graphs = 0;
 };
@@ -109,7 +110,7 @@ struct Resolved {
   uint32_t grain;
   int block;
   int blocks_per_sm;
-  bool nosync, timing, use_graph, l2_persist, stats;
+  bool nosync, timing, use_graph, l2_persist, stats, sym;
   uint64_t spin_limit, poison;
 };
 
@@ -135,6 +136,7 @@ mm_status resolve(const mm_graph* g, const mm_options* o, Resolved* r) {
   r->use_graph = o->use_graph != 0;
   r->l2_persist = o->l2_persist != 0;
   r->stats = o->stats != 0;
+  r->sym = o->symmetric != 0;
   r->spin_limit = o->spin_limit ? o->spin_limit : kDefaultSpin;
   r->poison = o->poison_vertex;
   if (r->poison > g->n) return fail(MM_ERR_ARG, "poison_vertex out of range");
@@ -174,6 +176,7 @@ SweepParams make_params(mm_graph* g, const Resolved& r, uint32_t* d_mate) {
   P.err = err_ptr(g);
   P.spin_limit = r.spin_limit;
   P.poison = r.poison;
+  P.sym = r.sym && !r.serial;
   return P;
 }
 
@@ -558,7 +561,7 @@ mm_status build_batch_graph(mm_graph* g, const Resolved& r, uint64_t num_graphs,
   b = BatchGraph{};
   CUDA_TRY(cudaGraphCreate(&b.graph, 0));
   const void *k_prepare = nullptr, *k_sweep = nullptr, *k_pairs = nullptr;
-  get_batched_kernels(r.bits, r.serial, &k_prepare, &k_sweep, &k_pairs);
+  get_batched_kernels(r.bits, r.serial, P.sym != 0, &k_prepare, &k_sweep, &k_pairs);
 
   SweepParams p = P;
   uint64_t* gp = graph_pairs;
@@ -605,6 +608,7 @@ mm_status build_batch_graph(mm_graph* g, const Resolved& r, uint64_t num_graphs,
   b.valid = true;
   b.status_bits = (uint32_t)r.bits;
   b.serial = r.serial;
+  b.sym = r.sym;
   b.grain = r.grain;
   b.block = (uint32_t)r.block;
   b.blocks_per_sm = (uint32_t)r.blocks_per_sm;
@@ -617,7 +621,7 @@ mm_status update_batch_graph(mm_graph* g, const Resolved& r, uint64_t num_graphs
                              const SweepParams& P, uint64_t* graph_pairs) {
   BatchGraph& b = g->bg;
   const void *k_prepare = nullptr, *k_sweep = nullptr, *k_pairs = nullptr;
-  get_batched_kernels(r.bits, r.serial, &k_prepare, &k_sweep, &k_pairs);
+  get_batched_kernels(r.bits, r.serial, P.sym != 0, &k_prepare, &k_sweep, &k_pairs);
   SweepParams p = P;
   uint64_t* gp = graph_pairs;
   uint64_t ng = num_graphs;
@@ -677,6 +681,7 @@ mm_status mm_skipper_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d_
     BatchGraph& b = g->bg;
     const bool with_pairs = d_graph_pairs != nullptr;
     const bool same = b.valid && b.status_bits == (uint32_t)r.bits && b.serial == (uint32_t)r.serial &&
+                      b.sym == r.sym &&
                       b.grain == r.grain && b.block == (uint32_t)r.block &&
                       b.blocks_per_sm == (uint32_t)r.blocks_per_sm && b.with_pairs == with_pairs &&
                       b.num_graphs == num_graphs && units <= g->part_units_cap;

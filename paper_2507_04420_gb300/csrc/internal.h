@@ -14,7 +14,7 @@ cudaError_t launch_prepare(const SweepParams& P, int bits, int grid, cudaStream_
 cudaError_t launch_sweep(const SweepParams& P, int bits, int grid, int block, cudaStream_t s);
 cudaError_t launch_serial(const SweepParams& P, int bits, cudaStream_t s);
 cudaError_t launch_serial_batched(const SweepParams& P, int bits, cudaStream_t s);
-void get_batched_kernels(int bits, bool serial, const void** prepare, const void** sweep,
+void get_batched_kernels(int bits, bool serial, bool sym, const void** prepare, const void** sweep,
                          const void** pairs);
 cudaError_t launch_graph_pairs(const uint32_t* mate, const int64_t* vbase, uint64_t num_graphs,
                                uint64_t n, uint64_t* graph_pairs, int grid, cudaStream_t s);

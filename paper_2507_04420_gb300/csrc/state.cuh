@@ -51,6 +51,9 @@ struct SweepParams {
   uint64_t num_graphs;
   // statistics (kStats kernels only): see StatSlot
   unsigned long long* stats;
+  // 1: the CSR is symmetric; an entry (x, y) with y < x is left to row y
+  // (selects the kSym kernel instance)
+  uint32_t sym;
 };
 
 // Sweep statistics, kept only by the kStats kernel instances.  A conflict is a

@@ -78,7 +78,7 @@ __global__ void prepare_kernel(SweepParams P, uint64_t* graph_pairs, uint64_t nu
   }
 }
 
-template <class S, bool kStats = false>
+template <class S, bool kStats = false, bool kSym = false>
 __global__ void __launch_bounds__(512, 3) sweep_kernel(SweepParams P) {
   const unsigned lane = threadIdx.x & 31u;
   const S s(P);
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(512, 3) sweep_kernel(SweepParams P) {
     const int64_t row0 = P.part[2 * w];
     const int64_t e_begin = P.part[2 * w + 1];
     const int64_t e_end = P.part[2 * w + 3];
-    if (e_begin < e_end) sweep_unit<S, kStats>(s, P, row0, e_begin, e_end, lane, pol);
+    if (e_begin < e_end) sweep_unit<S, kStats, kSym>(s, P, row0, e_begin, e_end, lane, pol);
     if ((w & 15) == 0) {  // stop handing out work once an error is recorded
       uint32_t e = 0;
       if (lane == 0) e = ld_relaxed(P.err);
@@ -168,8 +168,17 @@ cudaError_t launch_prepare(const SweepParams& P, int bits, int grid, cudaStream_
 
 cudaError_t launch_sweep(const SweepParams& P, int bits, int grid, int block, cudaStream_t s) {
   if (block > 512 || block < 32 || block % 32) return cudaErrorInvalidValue;
-  if (P.stats) {
+  // instances: statistics or not, symmetric filter or not
+  if (P.stats && P.sym) {
+#define L(S, B) (sweep_kernel<S, true, true><<<grid, block, 0, s>>>(P), 0)
+    SKP_DISPATCH_STATE(bits, L);
+#undef L
+  } else if (P.stats) {
 #define L(S, B) (sweep_kernel<S, true><<<grid, block, 0, s>>>(P), 0)
+    SKP_DISPATCH_STATE(bits, L);
+#undef L
+  } else if (P.sym) {
+#define L(S, B) (sweep_kernel<S, false, true><<<grid, block, 0, s>>>(P), 0)
     SKP_DISPATCH_STATE(bits, L);
 #undef L
   } else {
@@ -196,16 +205,19 @@ cudaError_t launch_serial_batched(const SweepParams& P, int bits, cudaStream_t s
   return cudaGetLastError();
 }
 
-void get_batched_kernels(int bits, bool serial, const void** prepare, const void** sweep,
+void get_batched_kernels(int bits, bool serial, bool sym, const void** prepare, const void** sweep,
                          const void** pairs) {
 #define PK(S, B) (const void*)prepare_kernel<B>
 #define SB(S, B) (const void*)serial_batched_kernel<S>
 #define SW(S, B) (const void*)sweep_kernel<S>
+#define SY(S, B) (const void*)sweep_kernel<S, false, true>
   *prepare = SKP_DISPATCH_STATE(bits, PK);
-  *sweep = serial ? SKP_DISPATCH_STATE(bits, SB) : SKP_DISPATCH_STATE(bits, SW);
+  *sweep = serial ? SKP_DISPATCH_STATE(bits, SB)
+                  : sym ? SKP_DISPATCH_STATE(bits, SY) : SKP_DISPATCH_STATE(bits, SW);
 #undef PK
 #undef SB
 #undef SW
+#undef SY
   *pairs = (const void*)graph_pairs_kernel;
 }
 

@@ -60,7 +60,7 @@ __device__ __forceinline__ int count_le(int rel, int p) {
 // read in chunks of up to 128 (one aligned 128-bit load per lane); the state
 // of the row at the head of each chunk is re-read alongside, so a long row
 // matched by another warp is left after at most one more chunk.
-template <class S, bool kStats = false>
+template <class S, bool kStats = false, bool kSym = false>
 __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int64_t row0,
                                            int64_t pos, const int64_t e_end, const unsigned lane,
                                            const uint64_t pol_stream) {
@@ -146,26 +146,26 @@ __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int
     head = __shfl_sync(kFull, head, 0);
     if (S::matched(head, x1)) mchd |= 1u << k1;
     if (lane == (unsigned)k1) my_st = head;
-    // words holding the row states, from the window snapshot
-    uint32_t rx[4], xs[4];
+    uint32_t xs[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      rx[j] = __shfl_sync(kFull, my_st, k[j] & 31);
-      xs[j] = (uint32_t)(wbase + k[j]);
-    }
+    for (int j = 0; j < 4; ++j) xs[j] = (uint32_t)(wbase + k[j]);
 
-    // filter (the line-10 read): candidates have both endpoints unmatched
+    // filter (the line-10 read): candidates have both endpoints unmatched.  A
+    // row whose snapshot word reads MCHD has its bit in mchd (set when the
+    // window or the head word was read), so the row test is the mask alone.
+    // Loops are skipped (lines 6-7); on a symmetric CSR so is every (x, y) with
+    // y < x, which row y holds as (y, x) (each edge tested once).
     bool want[4];
+    bool bad = false;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int p = p0 + j;
-      want[j] = p >= lo_r && p < hi_r && !(mchd >> (k[j] & 31) & 1u) && !S::matched(rx[j], xs[j]) &&
-                y[j] != xs[j];
-      if (want[j] && y[j] >= n32) {
-        atomicOr(P.err, kErrBadId);
-        want[j] = false;
-      }
+      want[j] = p >= lo_r && p < hi_r && !(mchd >> (k[j] & 31) & 1u) &&
+                (kSym ? y[j] > xs[j] : y[j] != xs[j]);
+      bad |= want[j] && y[j] >= n32;
+      want[j] = want[j] && y[j] < n32;
     }
+    if (__any_sync(kFull, bad) && bad) atomicOr(P.err, kErrBadId);
     uint32_t ry[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
     for (int j = 0; j < 4; ++j)
@@ -181,12 +181,13 @@ __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int
       if (!__any_sync(kFull, have)) break;
       const int j = have ? __ffs(cand) - 1 : 0;
       const uint32_t key = have ? pick4(xs, j) : kNone;
+      const uint32_t rxj = __shfl_sync(kFull, my_st, (key - (uint32_t)wbase) & 31);
       const unsigned peers = __match_any_sync(kFull, key);
       const int leader = __ffs(peers) - 1;
       unsigned done = 0u;
       if (have && (int)lane == leader) {
         cand &= ~(1u << j);
-        if (resolve_edge<S, kStats>(s, key, pick4(y, j), pick4(rx, j), pick4(ry, j), P))
+        if (resolve_edge<S, kStats>(s, key, pick4(y, j), rxj, pick4(ry, j), P))
           done = 1u << (key - (uint32_t)wbase);
       }
       done = __reduce_or_sync(kFull, done);  // rows that are now matched

@@ -158,6 +158,43 @@ def test_edges_stored_once(skp):
         assert np.array_equal(m, ref_mate)
 
 
+@pytest.mark.parametrize("bits", [2, 8, 32])
+def test_symmetric_option(skp, bits):
+    """symmetric=1: each edge tested once, from its lower endpoint's row; on a
+    symmetric CSR the result is a maximal matching like any other (verdicts
+    identical to the oracle's, sizes fixed where every maximal matching has
+    one size); serial mode ignores the option."""
+    for name in ("rmat10", "er2k", "grid16x32", "star64", "k3_17", "k9", "disjoint50", "path101"):
+        csr = SMALL[name]()
+        for grain in (128, 2048):
+            m, p, vr, vd = run(skp, csr, status_bits=bits, grain=grain, symmetric=1)
+            assert_parity(vr, vd)
+            fixed = {"star64": 1, "k3_17": 3, "k9": 4, "disjoint50": 50}
+            if name in fixed:
+                assert len(p) == fixed[name]
+        ref_mate, _ = oracle.sgmm(csr.offsets.numpy(), csr.nbrs.numpy())
+        m, p, vr, vd = run(skp, csr, status_bits=bits, serial=1, symmetric=1)
+        assert np.array_equal(m, ref_mate)
+    for bits_ in (bits,):
+        csr = gg.rmat(18, 16, seed=7)
+        m, p, vr, vd = run(skp, csr, status_bits=bits_, grain=8192, symmetric=1)
+        assert_parity(vr, vd)
+
+
+def test_symmetric_option_is_the_callers_promise(skp):
+    """On a CSR that holds each edge only in the row of its higher endpoint,
+    symmetric=1 leaves every entry to a row that does not hold it: nothing is
+    matched and the checker reports every entry uncovered."""
+    n = 50
+    csr = _manual(n, [[]] + [[i - 1] for i in range(1, n)])   # path, edge (i-1, i) in row i
+    m, p, vr, vd = run(skp, csr, symmetric=1)
+    assert m.tolist() == [NONE] * n and len(p) == 0
+    assert vr.flags == oracle.V_UNCOVERED and vr.n_uncovered == n - 1
+    assert vd.as_dict() == vr.as_dict()
+    m, p, vr, vd = run(skp, csr)                                 # without the promise: maximal
+    assert_parity(vr, vd)
+
+
 def test_empty_rows_and_tiny_graphs(skp):
     # long runs of isolated vertices between short rows
     n = 3000
