@@ -17,7 +17,7 @@
  * The library reads each stored entry (x, nbrs[i]) as the edge {x, nbrs[i]};
  * a graph stored once per direction (symmetric CSR) is the usual input, and
  * an edge stored for one endpoint only is matched all the same (Section V-C,
- * "Input Format & Symmetrization").  Self-loops are ignored (Algorithm 1
+ * the paragraph on input formats and symmetrisation).  Self-loops are ignored (Algorithm 1
  * skips them).  Vertex ids are uint32 with n <= 0xFFFFFFFD.
  *
  * Output: mate uint32_t[n] in device memory, mate[v] = the vertex matched to
