@@ -58,6 +58,7 @@ typedef enum mm_status {
 
 /* mm_create_csr flags */
 #define MM_CHECK_CSR 1u      /* check offsets and ids on the device (synchronous) */
+#define MM_HOST_MAPPED 2u    /* the input arrays are page-locked host memory, read in place */
 
 typedef struct mm_graph mm_graph;
 
@@ -200,6 +201,19 @@ mm_status mm_default_options(mm_options *o);
 mm_status mm_create_csr(uint64_t n, uint64_t nnz, const int64_t *d_offsets,
                         const uint32_t *d_nbrs, uint32_t flags, void *cuda_stream,
                         mm_graph **out);
+/*
+ * MM_HOST_MAPPED (mm_create_csr and mm_create_coo): the input arrays are host
+ * addresses -- page-locked memory (cudaHostAlloc, cudaHostRegister, a pinned
+ * torch tensor), or, on a device that reads pageable memory through the
+ * host's page tables (Grace-Blackwell), any host memory.  The handle takes
+ * their device addresses (cudaHostGetDevicePointer) and every kernel reads
+ * them in place through the host link -- NVLink-C2C on a Grace-Blackwell
+ * node -- so a call moves only what it reads: the sweep's row skip leaves
+ * most neighbour ids of a dense graph unread, which a copy of the whole CSR
+ * would move all the same.  The state array, the mate output and all scratch
+ * stay in device memory.  The arrays must stay valid and unchanged while the
+ * handle is used.  MM_ERR_ARG when the device cannot address an array.
+ */
 
 /*
  * Create a handle over an edge list in coordinate form (Section V-C: Skipper

@@ -76,20 +76,45 @@ def _need(t: torch.Tensor, name: str, dtypes):
 
 _U32 = tuple(d for d in (torch.int32, getattr(torch, "uint32", None)) if d is not None)
 
+MM_CHECK_CSR, MM_HOST_MAPPED = 1, 2
+
+
+def _need_pinned(t: torch.Tensor, name: str, dtypes):
+    """A host tensor in page-locked memory (read in place by the kernels)."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.is_cuda or not t.is_pinned():
+        raise ValueError(f"{name} must be a page-locked (pinned) host tensor for host_mapped")
+    if t.dtype not in dtypes:
+        raise TypeError(f"{name} must have dtype in {dtypes}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
 
 class Graph:
-    """A device CSR handle (mm_create_csr); borrows offsets/nbrs, which must outlive it."""
+    """A CSR handle (mm_create_csr); borrows offsets/nbrs, which must outlive it.
 
-    def __init__(self, offsets: torch.Tensor, nbrs: torch.Tensor, check: bool = True, stream=None):
-        _need(offsets, "offsets", (torch.int64,))
-        _need(nbrs, "nbrs", _U32)
+    The CSR is in device memory, or with host_mapped=True in page-locked host
+    memory that the kernels read in place (MM_HOST_MAPPED): a call then moves
+    over the host link only the entries it reads."""
+
+    def __init__(self, offsets: torch.Tensor, nbrs: torch.Tensor, check: bool = True, stream=None,
+                 host_mapped: bool = False):
+        if host_mapped:
+            _need_pinned(offsets, "offsets", (torch.int64,))
+            _need_pinned(nbrs, "nbrs", _U32)
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        else:
+            _need(offsets, "offsets", (torch.int64,))
+            _need(nbrs, "nbrs", _U32)
+            self.device = offsets.device
         self.offsets, self.nbrs = offsets, nbrs
-        self.device = offsets.device
         self.n = offsets.numel() - 1
         self.nnz = nbrs.numel()
+        flags = (MM_CHECK_CSR if check else 0) | (MM_HOST_MAPPED if host_mapped else 0)
         h = ctypes.c_void_p()
         _check(lib.mm_create_csr(self.n, self.nnz, _ptr(offsets), _ptr(nbrs) if self.nnz else None,
-                                 1 if check else 0, _stream_ptr(stream), ctypes.byref(h)),
+                                 flags, _stream_ptr(stream), ctypes.byref(h)),
                "mm_create_csr")
         self._h = h
 
@@ -204,18 +229,25 @@ class EdgeList(Graph):
     outlive it.  skipper / validate / stats / timing work as on a CSR handle;
     the batched calls do not apply."""
 
-    def __init__(self, n: int, src: torch.Tensor, dst: torch.Tensor, check: bool = True, stream=None):
-        _need(src, "src", _U32)
-        _need(dst, "dst", _U32)
+    def __init__(self, n: int, src: torch.Tensor, dst: torch.Tensor, check: bool = True, stream=None,
+                 host_mapped: bool = False):
+        if host_mapped:
+            _need_pinned(src, "src", _U32)
+            _need_pinned(dst, "dst", _U32)
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        else:
+            _need(src, "src", _U32)
+            _need(dst, "dst", _U32)
+            self.device = src.device
         if src.dim() != 1 or src.shape != dst.shape:
             raise ValueError("src and dst must be 1-D tensors of the same length")
         self.src, self.dst = src, dst
-        self.device = src.device
         self.n = int(n)
         self.nnz = self.m = src.numel()
+        flags = (MM_CHECK_CSR if check else 0) | (MM_HOST_MAPPED if host_mapped else 0)
         h = ctypes.c_void_p()
         _check(lib.mm_create_coo(self.n, self.m, _ptr(src) if self.m else None,
-                                 _ptr(dst) if self.m else None, 1 if check else 0,
+                                 _ptr(dst) if self.m else None, flags,
                                  _stream_ptr(stream), ctypes.byref(h)), "mm_create_coo")
         self._h = h
 
@@ -300,32 +332,51 @@ class Multi:
 class HostSession:
     """Skipper on graphs that live in host memory.
 
-    Keeps device buffers for up to (n_max, nnz_max) and one library handle;
-    each run() copies the CSR host->device, matches, and copies the mate
-    array back (pinned host tensors give asynchronous copies)."""
+    Two ways in.  zero_copy=True (the default) with page-locked (pinned) host
+    tensors: the kernels read the CSR in place through the host link
+    (MM_HOST_MAPPED), so a run moves only the offsets and the neighbour ids
+    the sweep reads -- on Grace-Blackwell over NVLink-C2C.  Otherwise (pageable
+    tensors, or zero_copy=False): the CSR is copied into device buffers kept
+    for up to (n_max, nnz_max).  Either way the mate array is computed in
+    device memory and copied back."""
 
-    def __init__(self, n_max: int, nnz_max: int, device=None):
+    def __init__(self, n_max: int, nnz_max: int, device=None, zero_copy: bool = True):
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.n_max, self.nnz_max = n_max, nnz_max
-        self.d_off = torch.zeros(n_max + 1, dtype=torch.int64, device=dev)
-        self.d_nb = torch.empty(max(nnz_max, 4), dtype=torch.int32, device=dev)
+        self.zero_copy = zero_copy
+        self.dev = dev
+        self.d_off = self.d_nb = None       # copy-path buffers, made on first use
         self.d_mate = torch.empty(max(n_max, 1), dtype=torch.int32, device=dev)
         self._graphs = {}
         self.last_verdict = None
+        self.last_mode = None
 
     def run(self, offsets: torch.Tensor, nbrs: torch.Tensor, mate_out: Optional[torch.Tensor] = None,
             stream=None, check: bool = False, **kw) -> torch.Tensor:
         n, nnz = offsets.numel() - 1, nbrs.numel()
         if n > self.n_max or nnz > self.nnz_max:
             raise ValueError("graph larger than the session's buffers")
-        off_d, nb_d, mate_d = self.d_off[: n + 1], self.d_nb[:nnz], self.d_mate[:n]
-        off_d.copy_(offsets, non_blocking=True)
-        nb_d.copy_(nbrs, non_blocking=True)
-        key = (n, nnz)
-        g = self._graphs.get(key)
-        if g is None:  # the handle only borrows the buffers; their contents change per run
-            self.close()
-            g = self._graphs[key] = Graph(off_d, nb_d, check=False, stream=stream)
+        mate_d = self.d_mate[:n]
+        if self.zero_copy and offsets.is_pinned() and (nnz == 0 or nbrs.is_pinned()):
+            self.last_mode = "host_mapped"
+            key = ("mapped", offsets.data_ptr(), nbrs.data_ptr(), n, nnz)
+            g = self._graphs.get(key)
+            if g is None:  # one handle per pair of host arrays (mapped in place)
+                self.close()
+                g = self._graphs[key] = Graph(offsets, nbrs, check=False, stream=stream, host_mapped=True)
+        else:
+            self.last_mode = "copy"
+            if self.d_off is None:
+                self.d_off = torch.zeros(self.n_max + 1, dtype=torch.int64, device=self.dev)
+                self.d_nb = torch.empty(max(self.nnz_max, 4), dtype=torch.int32, device=self.dev)
+            off_d, nb_d = self.d_off[: n + 1], self.d_nb[:nnz]
+            off_d.copy_(offsets, non_blocking=True)
+            nb_d.copy_(nbrs, non_blocking=True)
+            key = ("copy", n, nnz)
+            g = self._graphs.get(key)
+            if g is None:  # the handle only borrows the buffers; their contents change per run
+                self.close()
+                g = self._graphs[key] = Graph(off_d, nb_d, check=False, stream=stream)
         g.skipper(mate=mate_d, stream=stream, **kw)
         self.last_verdict = g.validate(mate_d, stream=stream) if check else None
         if mate_out is None:

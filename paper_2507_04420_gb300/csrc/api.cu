@@ -262,6 +262,22 @@ mm_status read_slot(mm_graph* g, uint32_t slot, mm_timing* out) {
   return MM_OK;
 }
 
+// MM_HOST_MAPPED: the device address of host memory (page-locked, or any
+// host memory on a device that walks the host's page tables; the same address
+// under unified addressing); MM_ERR_ARG when the device cannot address it.
+template <class T>
+mm_status map_host(const T** p, const char* what) {
+  void* d = nullptr;
+  const cudaError_t e = cudaHostGetDevicePointer(&d, const_cast<T*>(*p), 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // not sticky; clear it for the caller's next call
+    return fail(MM_ERR_ARG, "%s is host memory the device cannot address (MM_HOST_MAPPED): %s",
+                what, cudaGetErrorString(e));
+  }
+  *p = static_cast<const T*>(d);
+  return MM_OK;
+}
+
 mm_status check_handle(const mm_graph* g) {
   if (!g) return fail(MM_ERR_ARG, "null handle");
   int dev = -1;
@@ -347,12 +363,23 @@ mm_status mm_create_coo(uint64_t n, uint64_t m, const uint32_t* d_src, const uin
   *out = nullptr;
   if (n > MM_MAX_VERTICES) return fail(MM_ERR_ARG, "n = %llu exceeds %llu", (unsigned long long)n, MM_MAX_VERTICES);
   if (m && (!d_src || !d_dst)) return fail(MM_ERR_ARG, "null src / dst with m > 0");
-  if ((reinterpret_cast<uintptr_t>(d_src) | reinterpret_cast<uintptr_t>(d_dst)) & 3u)
-    return fail(MM_ERR_ARG, "src and dst must be 4-byte aligned");
-  if (flags & ~MM_CHECK_CSR) return fail(MM_ERR_ARG, "unknown flags 0x%x", flags);
+  auto aligned = [&]() {
+    if ((reinterpret_cast<uintptr_t>(d_src) | reinterpret_cast<uintptr_t>(d_dst)) & 3u)
+      return fail(MM_ERR_ARG, "src and dst must be 4-byte aligned");
+    return MM_OK;
+  };
+  mm_status ms = (flags & MM_HOST_MAPPED) ? MM_OK : aligned();
+  if (ms != MM_OK) return ms;
+  if (flags & ~(MM_CHECK_CSR | MM_HOST_MAPPED)) return fail(MM_ERR_ARG, "unknown flags 0x%x", flags);
   int ndev = 0;
   CUDA_TRY(cudaGetDeviceCount(&ndev));
   if (ndev <= 0) return fail(MM_ERR_CUDA, "no CUDA device");
+  if ((flags & MM_HOST_MAPPED) && m) {  // the device addresses of the caller's page-locked arrays
+    ms = map_host(&d_src, "src");
+    if (ms == MM_OK) ms = map_host(&d_dst, "dst");
+    if (ms == MM_OK) ms = aligned();
+    if (ms != MM_OK) return ms;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
 
   mm_graph* g = new (std::nothrow) mm_graph();
@@ -407,13 +434,24 @@ mm_status mm_create_csr(uint64_t n, uint64_t nnz, const int64_t* d_offsets, cons
   if (n > MM_MAX_VERTICES) return fail(MM_ERR_ARG, "n = %llu exceeds %llu", (unsigned long long)n, MM_MAX_VERTICES);
   if (!d_offsets) return fail(MM_ERR_ARG, "null offsets");
   if (nnz && !d_nbrs) return fail(MM_ERR_ARG, "null nbrs with nnz > 0");
-  if (nnz && (reinterpret_cast<uintptr_t>(d_nbrs) & 15u))
-    return fail(MM_ERR_ARG, "nbrs must be 16-byte aligned");
-  if (reinterpret_cast<uintptr_t>(d_offsets) & 7u) return fail(MM_ERR_ARG, "offsets must be 8-byte aligned");
-  if (flags & ~MM_CHECK_CSR) return fail(MM_ERR_ARG, "unknown flags 0x%x", flags);
+  auto aligned = [&]() {
+    if (nnz && (reinterpret_cast<uintptr_t>(d_nbrs) & 15u))
+      return fail(MM_ERR_ARG, "nbrs must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(d_offsets) & 7u) return fail(MM_ERR_ARG, "offsets must be 8-byte aligned");
+    return MM_OK;
+  };
+  mm_status ms = (flags & MM_HOST_MAPPED) ? MM_OK : aligned();
+  if (ms != MM_OK) return ms;
+  if (flags & ~(MM_CHECK_CSR | MM_HOST_MAPPED)) return fail(MM_ERR_ARG, "unknown flags 0x%x", flags);
   int ndev = 0;
   CUDA_TRY(cudaGetDeviceCount(&ndev));
   if (ndev <= 0) return fail(MM_ERR_CUDA, "no CUDA device");
+  if (flags & MM_HOST_MAPPED) {  // the device addresses of the caller's page-locked arrays
+    ms = map_host(&d_offsets, "offsets");
+    if (ms == MM_OK && nnz) ms = map_host(&d_nbrs, "nbrs");
+    if (ms == MM_OK) ms = aligned();
+    if (ms != MM_OK) return ms;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
 
   mm_graph* g = new (std::nothrow) mm_graph();
