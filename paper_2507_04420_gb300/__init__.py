@@ -12,6 +12,7 @@ an unmatched vertex reads as -1 (0xFFFFFFFF).
 """
 from __future__ import annotations
 
+import collections
 import ctypes
 from typing import Optional
 
@@ -333,12 +334,15 @@ class HostSession:
     """Skipper on graphs that live in host memory.
 
     Two ways in.  zero_copy=True (the default) with page-locked (pinned) host
-    tensors: the kernels read the CSR in place through the host link
-    (MM_HOST_MAPPED), so a run moves only the offsets and the neighbour ids
-    the sweep reads -- on Grace-Blackwell over NVLink-C2C.  Otherwise (pageable
-    tensors, or zero_copy=False): the CSR is copied into device buffers kept
-    for up to (n_max, nnz_max).  Either way the mate array is computed in
-    device memory and copied back."""
+    tensors and no check: the kernels read the CSR in place through the host
+    link (MM_HOST_MAPPED), so a run moves only the offsets and the neighbour
+    ids the sweep reads -- on Grace-Blackwell over NVLink-C2C.  Otherwise
+    (pageable tensors, zero_copy=False, or check=True, whose checker reads
+    every entry and is better served by one bulk copy): the CSR is copied into
+    device buffers kept for up to (n_max, nnz_max).  Either way the mate array
+    is computed in device memory and copied back."""
+
+    MAPPED_HANDLES = 4   # host-mapped handles kept (least recently used first out)
 
     def __init__(self, n_max: int, nnz_max: int, device=None, zero_copy: bool = True):
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -347,7 +351,8 @@ class HostSession:
         self.dev = dev
         self.d_off = self.d_nb = None       # copy-path buffers, made on first use
         self.d_mate = torch.empty(max(n_max, 1), dtype=torch.int32, device=dev)
-        self._graphs = {}
+        self._graphs = {}          # the copy-path handle, keyed by (n, nnz)
+        self._mapped = collections.OrderedDict()   # host-mapped handles, keyed by the host arrays
         self.last_verdict = None
         self.last_mode = None
 
@@ -357,13 +362,16 @@ class HostSession:
         if n > self.n_max or nnz > self.nnz_max:
             raise ValueError("graph larger than the session's buffers")
         mate_d = self.d_mate[:n]
-        if self.zero_copy and offsets.is_pinned() and (nnz == 0 or nbrs.is_pinned()):
+        if self.zero_copy and not check and offsets.is_pinned() and (nnz == 0 or nbrs.is_pinned()):
             self.last_mode = "host_mapped"
-            key = ("mapped", offsets.data_ptr(), nbrs.data_ptr(), n, nnz)
-            g = self._graphs.get(key)
-            if g is None:  # one handle per pair of host arrays (mapped in place)
-                self.close()
-                g = self._graphs[key] = Graph(offsets, nbrs, check=False, stream=stream, host_mapped=True)
+            key = (offsets.data_ptr(), nbrs.data_ptr(), n, nnz)
+            g = self._mapped.get(key)
+            if g is None:  # one handle per pair of host arrays (read in place)
+                g = Graph(offsets, nbrs, check=False, stream=stream, host_mapped=True)
+                self._mapped[key] = g
+                while len(self._mapped) > self.MAPPED_HANDLES:
+                    self._mapped.popitem(last=False)[1].close()
+            self._mapped.move_to_end(key)
         else:
             self.last_mode = "copy"
             if self.d_off is None:
@@ -372,10 +380,12 @@ class HostSession:
             off_d, nb_d = self.d_off[: n + 1], self.d_nb[:nnz]
             off_d.copy_(offsets, non_blocking=True)
             nb_d.copy_(nbrs, non_blocking=True)
-            key = ("copy", n, nnz)
+            key = (n, nnz)
             g = self._graphs.get(key)
             if g is None:  # the handle only borrows the buffers; their contents change per run
-                self.close()
+                for old in self._graphs.values():
+                    old.close()
+                self._graphs.clear()
                 g = self._graphs[key] = Graph(off_d, nb_d, check=False, stream=stream)
         g.skipper(mate=mate_d, stream=stream, **kw)
         self.last_verdict = g.validate(mate_d, stream=stream) if check else None
@@ -386,6 +396,7 @@ class HostSession:
         return mate_out
 
     def close(self):
-        for g in self._graphs.values():
+        for g in list(self._graphs.values()) + list(self._mapped.values()):
             g.close()
         self._graphs.clear()
+        self._mapped.clear()

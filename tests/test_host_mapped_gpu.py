@@ -76,8 +76,8 @@ def test_host_session_zero_copy_and_copy_agree(skp):
             assert cp.last_mode == "copy"
             assert np.array_equal(a.numpy().view(np.uint32), ref)
             assert np.array_equal(b.numpy().view(np.uint32), ref)
-            m = zc.run(off, nb, check=True)
-            assert zc.last_verdict.flags == 0
+            m = zc.run(off, nb, check=True)     # the checker reads every entry: copied in bulk
+            assert zc.last_mode == "copy" and zc.last_verdict.flags == 0
             assert oracle.check(g.offsets.numpy(), g.nbrs.numpy(), m.numpy().view(np.uint32)).flags == 0
         # pageable tensors fall back to the copy path
         g = graphs[0]
