@@ -238,6 +238,16 @@ mm_status mm_create_coo(uint64_t n, uint64_t m, const uint32_t *d_src, const uin
                         uint32_t flags, void *cuda_stream, mm_graph **out);
 
 /*
+ * The device address of host memory that kernels can read in place: the
+ * lookup MM_HOST_MAPPED makes (page-locked memory, or any host memory on a
+ * device that walks the host's page tables), for callers who fill
+ * mm_graph_desc entries themselves.  Writes it to *device_out.  No paper
+ * counterpart: it exists for the host-resident inputs of this library.
+ * Errors: MM_ERR_ARG (null argument, or memory the device cannot address).
+ */
+mm_status mm_host_device_address(const void *host, const void **device_out);
+
+/*
  * Skipper's single pass (Algorithm 1): every vertex starts ACC (lines 3-4);
  * every stored entry (x, y), x != y, is resolved once with u = min(x, y),
  * v = max(x, y): reserve u ACC->RSVD, claim v ACC->MCHD, then set u MCHD or

@@ -21,7 +21,7 @@ import torch
 from . import _native
 from ._native import GraphDesc, Options, Stats, Timing, Verdict
 
-__all__ = ["EdgeList", "Graph", "HostSession", "Multi", "SkipperError", "match", "validate", "Options", "Verdict", "Timing",
+__all__ = ["EdgeList", "Graph", "device_address", "HostSession", "Multi", "SkipperError", "match", "validate", "Options", "Verdict", "Timing",
            "UNMATCHED", "lib", "options"]
 
 UNMATCHED = 0xFFFFFFFF
@@ -264,12 +264,26 @@ def validate(offsets: torch.Tensor, nbrs: torch.Tensor, mate: torch.Tensor, pair
         return g.validate(mate, pairs)
 
 
+def device_address(t: torch.Tensor) -> int:
+    """Device address of a tensor's memory: its data pointer for a CUDA tensor,
+    the in-place address (mm_host_device_address) for a host tensor."""
+    if t.is_cuda:
+        return t.data_ptr()
+    out = ctypes.c_void_p()
+    _check(lib.mm_host_device_address(ctypes.c_void_p(t.data_ptr()), ctypes.byref(out)),
+           "mm_host_device_address")
+    return int(out.value)
+
+
 class Multi:
     """Many independent graphs, each in its own device tensors, matched in one
     launch (mm_skipper_multi) and checked in one launch (mm_validate_multi).
 
     A graph is a tuple (offsets int64[n+1], nbrs int32[nnz], mate int32[n]) of
-    CUDA tensors; calls on one Multi must be ordered (one stream)."""
+    CUDA tensors; with allow_host=True offsets and nbrs may also be pinned
+    host tensors, which the kernels read in place (the device addresses of
+    page-locked memory are its host addresses under unified addressing).
+    Calls on one Multi must be ordered (one stream)."""
 
     def __init__(self):
         h = ctypes.c_void_p()
@@ -277,38 +291,52 @@ class Multi:
         self._h = h
 
     @staticmethod
-    def _descs(graphs):
+    def _descs(graphs, allow_host: bool = False):
         arr = (GraphDesc * max(1, len(graphs)))()
         for i, (off, nb, mate) in enumerate(graphs):
-            _need(off, "offsets", (torch.int64,))
-            _need(nb, "nbrs", _U32)
+            if allow_host and not off.is_cuda:
+                _need_pinned(off, "offsets", (torch.int64,))
+                _need_pinned(nb, "nbrs", _U32)
+            else:
+                _need(off, "offsets", (torch.int64,))
+                _need(nb, "nbrs", _U32)
             _need(mate, "mate", _U32)
             arr[i].n = off.numel() - 1
             arr[i].nnz = nb.numel()
-            arr[i].offsets = off.data_ptr()
-            arr[i].nbrs = nb.data_ptr() if nb.numel() else None
+            arr[i].offsets = device_address(off)
+            arr[i].nbrs = device_address(nb) if nb.numel() else None
             arr[i].mate = mate.data_ptr() if mate.numel() else None
         return arr
 
-    def run(self, graphs, stream=None, opts: Optional[Options] = None, **kw):
+    def run_descs(self, arr, count: int, stream=None, opts: Optional[Options] = None, **kw):
+        """mm_skipper_multi over a GraphDesc array the caller filled (device addresses)."""
         o = opts if opts is not None else options(**kw)
-        arr = self._descs(graphs)
+        _check(lib.mm_skipper_multi(self._h, count, arr, ctypes.byref(o), _stream_ptr(stream)),
+               "mm_skipper_multi")
+
+    def validate_async_descs(self, arr, count: int, stream=None):
+        _check(lib.mm_validate_multi_async(self._h, count, arr, _stream_ptr(stream)),
+               "mm_validate_multi_async")
+
+    def run(self, graphs, stream=None, opts: Optional[Options] = None, allow_host: bool = False, **kw):
+        o = opts if opts is not None else options(**kw)
+        arr = self._descs(graphs, allow_host)
         _check(lib.mm_skipper_multi(self._h, len(graphs), arr, ctypes.byref(o), _stream_ptr(stream)),
                "mm_skipper_multi")
 
     def sync(self, stream=None):
         _check(lib.mm_multi_sync(self._h, _stream_ptr(stream)), "mm_multi_sync")
 
-    def validate(self, graphs, stream=None):
-        arr = self._descs(graphs)
+    def validate(self, graphs, stream=None, allow_host: bool = False):
+        arr = self._descs(graphs, allow_host)
         out = (Verdict * max(1, len(graphs)))()
         _check(lib.mm_validate_multi(self._h, len(graphs), arr, out, _stream_ptr(stream)),
                "mm_validate_multi")
         return [out[i] for i in range(len(graphs))]
 
-    def validate_async(self, graphs, stream=None):
+    def validate_async(self, graphs, stream=None, allow_host: bool = False):
         """Enqueue the checker for these graphs on the stream (after a run on it)."""
-        arr = self._descs(graphs)
+        arr = self._descs(graphs, allow_host)
         _check(lib.mm_validate_multi_async(self._h, len(graphs), arr, _stream_ptr(stream)),
                "mm_validate_multi_async")
 

@@ -161,6 +161,7 @@ SYMBOLS = [
     ("mm_default_options", _I, [ctypes.POINTER(Options)]),
     ("mm_create_csr", _I, [_U64, _U64, _P, _P, _U32, _P, ctypes.POINTER(_P)]),
     ("mm_create_coo", _I, [_U64, _U64, _P, _P, _U32, _P, ctypes.POINTER(_P)]),
+    ("mm_host_device_address", _I, [_P, ctypes.POINTER(_P)]),
     ("mm_skipper", _I, [_P, ctypes.POINTER(Options), _P, _P, _U64, _P, _P]),
     ("mm_skipper_batched", _I, [_P, _U64, _P, _P, ctypes.POINTER(Options), _P, _P, _P]),
     ("mm_validate", _I, [_P, _P, _P, _U64, ctypes.POINTER(Verdict), _P]),

@@ -356,6 +356,16 @@ mm_status mm_default_options(mm_options* o) {
   return MM_OK;
 }
 
+mm_status mm_host_device_address(const void* host, const void** device_out) {
+  g_err[0] = 0;
+  if (!host || !device_out) return fail(MM_ERR_ARG, "null argument");
+  const unsigned char* p = static_cast<const unsigned char*>(host);
+  mm_status st = map_host(&p, "host address");
+  if (st != MM_OK) return st;
+  *device_out = p;
+  return MM_OK;
+}
+
 mm_status mm_create_coo(uint64_t n, uint64_t m, const uint32_t* d_src, const uint32_t* d_dst,
                         uint32_t flags, void* cuda_stream, mm_graph** out) {
   g_err[0] = 0;

@@ -1,14 +1,22 @@
 """Continuous-batching Skipper server on one GPU.
 
 Requests (graphs in host memory) arrive at any time.  A worker thread admits
-them in arrival order while their device footprint fits the memory budget,
-copies each CSR to its own device buffers on a copy stream (the CSR and the
-state stay resident until the request completes), and whenever a compute slot
-is free launches one multi-graph pass (mm_skipper_multi) over every request
-admitted since the last launch.  Two compute slots alternate, so a new batch
-is admitted, copied and launched while the previous one is still on the GPU.
-Each result is checked by the exact device checker (mm_validate_multi) before
-its request completes; its mate array is copied back on a second copy stream.
+them in arrival order while their device footprint fits the memory budget and
+whenever a compute slot is free launches one multi-graph pass
+(mm_skipper_multi) over every request admitted since the last launch.  Two
+compute slots alternate, so a new batch is admitted and launched while the
+previous one is still on the GPU.  Each result is checked by the exact device
+checker (mm_validate_multi) before its request completes; its mate array is
+copied back on a second copy stream.
+
+A request reaches the GPU one of two ways.  Small requests in page-locked
+memory (up to in_place_max_nnz entries) are read in place: the kernels read
+their CSR through the host link (their device addresses come from
+mm_host_device_address on the client thread), and their mate arrays share one
+device arena per launch -- no device allocation and no host->device copy per
+request.  Larger ones are copied to their own device buffers on a copy stream
+(their checker reads every entry, which one bulk copy serves best); the CSR and
+the state stay resident until the request completes.
 
 Latency of a request = completion (mate in host memory, verdict known) minus
 submission.
@@ -23,18 +31,20 @@ from typing import List, Optional, Sequence, Tuple
 
 import torch
 
-from . import Multi, SkipperError, options
+from . import GraphDesc, Multi, SkipperError, device_address, options
 
 __all__ = ["Request", "Server", "device_bytes", "plan_admission"]
 
 
-def device_bytes(n: int, nnz: int) -> int:
-    """Device memory a request holds while resident: offsets, neighbour ids and
-    mate, plus its share of the launch scratch (packed states, partition and
-    unit tables, the checker's marks), rounded up to 512-byte granules."""
+def device_bytes(n: int, nnz: int, in_place: bool = False) -> int:
+    """Device memory a request holds while resident: offsets and neighbour ids
+    (not when read in place), mate, plus its share of the launch scratch
+    (packed states, partition and unit tables, the checker's marks), rounded
+    up to 512-byte granules."""
     r = lambda b: (b + 511) // 512 * 512
     scratch = (n // 4 + 8) + n + 24 * ((n + nnz) // 1024 + 2)
-    return r(8 * (n + 1)) + r(4 * max(nnz, 1)) + r(4 * max(n, 1)) + r(scratch)
+    csr = 0 if in_place else r(8 * (n + 1)) + r(4 * max(nnz, 1))
+    return csr + r(4 * max(n, 1)) + r(scratch)
 
 
 def plan_admission(sizes: Sequence[int], used: int, budget: int, max_graphs: int) -> Tuple[int, int]:
@@ -54,9 +64,9 @@ def plan_admission(sizes: Sequence[int], used: int, budget: int, max_graphs: int
 
 class Request:
     __slots__ = ("rid", "offsets", "nbrs", "n", "nnz", "arrival", "done_t", "mate", "verdict",
-                 "error", "_event", "_dev", "_bytes", "tick")
+                 "error", "in_place", "_event", "_dev", "_addr", "_mate_d", "_bytes", "tick")
 
-    def __init__(self, rid: int, offsets: torch.Tensor, nbrs: torch.Tensor):
+    def __init__(self, rid: int, offsets: torch.Tensor, nbrs: torch.Tensor, in_place: bool = False):
         self.rid = rid
         self.offsets, self.nbrs = offsets, nbrs
         self.n, self.nnz = offsets.numel() - 1, nbrs.numel()
@@ -65,9 +75,12 @@ class Request:
         self.mate = None
         self.verdict = None
         self.error = None
+        self.in_place = in_place
         self._event = threading.Event()
         self._dev = None
-        self._bytes = device_bytes(self.n, self.nnz)
+        self._addr = None      # (offsets, nbrs) device addresses when read in place
+        self._mate_d = None    # device mate (a slice of the launch's arena when read in place)
+        self._bytes = device_bytes(self.n, self.nnz, in_place)
         self.tick = None
 
     def wait(self, timeout: Optional[float] = None) -> bool:
@@ -82,13 +95,14 @@ class Server:
     def __init__(self, device=None, memory_bytes: Optional[int] = None, reserve_bytes: int = 8 << 30,
                  max_graphs_per_tick: int = 4096, max_bytes_per_tick: int = 32 << 30,
                  status_bits: int = 32, grain: int = 2048, serial: bool = False,
-                 validate: bool = True, slots: int = 2):
+                 validate: bool = True, slots: int = 2, in_place_max_nnz: int = 1 << 20):
         self.dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         free, _ = torch.cuda.mem_get_info(self.dev)
         self.budget = memory_bytes if memory_bytes is not None else max(0, free - reserve_bytes)
         self.max_graphs = max_graphs_per_tick
         self.max_tick_bytes = max_bytes_per_tick
         self.validate = validate
+        self.in_place_max_nnz = in_place_max_nnz
         self.opts = options(status_bits=status_bits, grain=grain, serial=int(serial), nosync=1)
         self.h2d = torch.cuda.Stream(self.dev)
         self.d2h = torch.cuda.Stream(self.dev)
@@ -122,7 +136,13 @@ class Server:
         with self._lock:
             rid = self._rid
             self._rid += 1
-        req = Request(rid, offsets, nbrs)
+        nnz = nbrs.numel()
+        in_place = (nnz <= self.in_place_max_nnz and offsets.is_pinned() and (nnz == 0 or nbrs.is_pinned())
+                    and offsets.dtype == torch.int64 and nbrs.dtype in (torch.int32,)
+                    and offsets.is_contiguous() and nbrs.is_contiguous())
+        req = Request(rid, offsets, nbrs, in_place)
+        if in_place:   # resolved here, on the client thread
+            req._addr = (device_address(offsets), device_address(nbrs) if nnz else 0)
         req.mate = mate_out
         if self.error is not None:
             req.error = self.error
@@ -147,6 +167,8 @@ class Server:
 
     # -- worker -------------------------------------------------------------------
     def _admit(self, req: Request):
+        if req.in_place:       # its mate is carved from the launch's arena
+            return
         with torch.cuda.stream(self.h2d):
             off = torch.empty(req.n + 1, dtype=torch.int64, device=self.dev)
             nb = torch.empty(max(req.nnz, 1), dtype=torch.int32, device=self.dev)[: req.nnz]
@@ -155,6 +177,7 @@ class Server:
             if req.nnz:
                 nb.copy_(req.nbrs, non_blocking=True)
         req._dev = (off, nb, mate)
+        req._mate_d = mate
 
     def _launch(self, batch: List[Request]):
         stream, multi = self.slots[self._next_slot]
@@ -163,24 +186,47 @@ class Server:
         copied = torch.cuda.Event()
         copied.record(self.h2d)
         stream.wait_event(copied)
-        graphs = [r._dev for r in batch]
-        multi.run(graphs, stream=stream, opts=self.opts)
+        arena = None
+        total = sum(r.n for r in batch if r.in_place)
+        if total:  # one device allocation for the mates of all in-place requests
+            with torch.cuda.stream(stream):
+                arena = torch.empty(total, dtype=torch.int32, device=self.dev)
+            at = 0
+            for r in batch:
+                if r.in_place:
+                    r._mate_d = arena[at:at + r.n]
+                    at += r.n
+        arr = (GraphDesc * max(1, len(batch)))()
+        for i, r in enumerate(batch):
+            d = arr[i]
+            d.n, d.nnz = r.n, r.nnz
+            if r.in_place:
+                d.offsets, d.nbrs = r._addr[0], (r._addr[1] or None)
+            else:
+                d.offsets, d.nbrs = r._dev[0].data_ptr(), (r._dev[1].data_ptr() if r.nnz else None)
+            d.mate = r._mate_d.data_ptr() if r.n else None
+        multi.run_descs(arr, len(batch), stream=stream, opts=self.opts)
         swept = torch.cuda.Event()
         swept.record(stream)
         if self.validate:  # the checker runs behind the pass, on the same stream
-            multi.validate_async(graphs, stream=stream)
+            multi.validate_async_descs(arr, len(batch), stream=stream)
         checked = torch.cuda.Event()
         checked.record(stream)
         for r in batch:  # the device tensors were made on the copy stream; they are used here too
-            for t in r._dev:
-                t.record_stream(stream)
+            if r._dev is not None:
+                for t in r._dev:
+                    t.record_stream(stream)
         self.d2h.wait_event(swept)
         with torch.cuda.stream(self.d2h):
             for r in batch:
                 if r.mate is None:
                     r.mate = torch.empty(r.n, dtype=torch.int32, pin_memory=True)
-                r.mate.copy_(r._dev[2], non_blocking=True)
-                r._dev[2].record_stream(self.d2h)
+                r.mate.copy_(r._mate_d, non_blocking=True)
+            if arena is not None:
+                arena.record_stream(self.d2h)
+            for r in batch:
+                if r._dev is not None:
+                    r._dev[2].record_stream(self.d2h)
         back = torch.cuda.Event()
         back.record(self.d2h)
         self.ticks += 1
@@ -204,6 +250,7 @@ class Server:
             r.error = err
             r.done_t = now
             r._dev = None
+            r._mate_d = None
             self.used -= r._bytes
             r._event.set()
         return True

@@ -85,8 +85,9 @@ def _pinned(g):
     return g.offsets.pin_memory(), g.nbrs.pin_memory()
 
 
+@pytest.mark.parametrize("in_place_max_nnz", [0, 20000, 1 << 20])   # all copied, mixed, all in place
 @pytest.mark.parametrize("serial", [1, 0])
-def test_server_results_same_alone_and_in_the_mix(skp, graphs, serial):
+def test_server_results_same_alone_and_in_the_mix(skp, graphs, serial, in_place_max_nnz):
     from paper_2507_04420_gb300.server import Server
     alone = []
     for g in graphs:
@@ -96,7 +97,8 @@ def test_server_results_same_alone_and_in_the_mix(skp, graphs, serial):
     # a small memory budget forces several admission rounds, and staggered
     # submissions make requests join while earlier ones are on the GPU
     budget = max(4 * 1024 * 1024, 3 * max(g.nnz * 4 + g.n * 12 for g in graphs))
-    srv = Server(memory_bytes=budget, serial=bool(serial), status_bits=32)
+    srv = Server(memory_bytes=budget, serial=bool(serial), status_bits=32,
+                 in_place_max_nnz=in_place_max_nnz)
     reqs = []
 
     def client():
@@ -113,6 +115,7 @@ def test_server_results_same_alone_and_in_the_mix(skp, graphs, serial):
         assert r.wait(120)
     srv.close()
     assert srv.ticks > 1
+    assert all(r.in_place == (g.nnz <= in_place_max_nnz) for g, r in reqs)
     for idx, (g, r) in enumerate(reqs):
         assert r.error is None
         m = r.mate.numpy().view(np.uint32)
@@ -124,12 +127,19 @@ def test_server_results_same_alone_and_in_the_mix(skp, graphs, serial):
 
 
 def test_server_rejects_what_can_never_fit(skp):
-    from paper_2507_04420_gb300.server import Server
-    srv = Server(memory_bytes=1 << 20)
+    from paper_2507_04420_gb300.server import Server, device_bytes
     g = gg.rmat(14, 16, seed=2)
+    assert device_bytes(g.n, g.nnz) > (1 << 20) > device_bytes(g.n, g.nnz, in_place=True)
+    srv = Server(memory_bytes=1 << 20, in_place_max_nnz=0)   # every request copied
     r = srv.submit(*_pinned(g))
     assert r.wait(5) and isinstance(r.error, MemoryError)
     small = gg.path(100)
     r2 = srv.submit(*_pinned(small))
     assert r2.wait(60) and r2.error is None and r2.verdict.flags == 0
+    srv.close()
+    srv = Server(memory_bytes=1 << 20)                       # read in place, the CSR stays on the host
+    r3 = srv.submit(*_pinned(g))
+    assert r3.wait(60) and r3.error is None and r3.in_place and r3.verdict.flags == 0
+    vr = oracle.check(g.offsets.numpy(), g.nbrs.numpy(), r3.mate.numpy().view(np.uint32))
+    assert vr.flags == 0 and vr.as_dict() == r3.verdict.as_dict()
     srv.close()
