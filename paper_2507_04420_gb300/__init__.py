@@ -370,7 +370,7 @@ class HostSession:
     device buffers kept for up to (n_max, nnz_max).  Either way the mate array
     is computed in device memory and copied back."""
 
-    MAPPED_HANDLES = 4   # host-mapped handles kept (least recently used first out)
+    HANDLES = 16   # handles kept per way in (least recently used first out)
 
     def __init__(self, n_max: int, nnz_max: int, device=None, zero_copy: bool = True):
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -379,7 +379,7 @@ class HostSession:
         self.dev = dev
         self.d_off = self.d_nb = None       # copy-path buffers, made on first use
         self.d_mate = torch.empty(max(n_max, 1), dtype=torch.int32, device=dev)
-        self._graphs = {}          # the copy-path handle, keyed by (n, nnz)
+        self._graphs = collections.OrderedDict()   # copy-path handles, keyed by (n, nnz)
         self._mapped = collections.OrderedDict()   # host-mapped handles, keyed by the host arrays
         self.last_verdict = None
         self.last_mode = None
@@ -397,7 +397,7 @@ class HostSession:
             if g is None:  # one handle per pair of host arrays (read in place)
                 g = Graph(offsets, nbrs, check=False, stream=stream, host_mapped=True)
                 self._mapped[key] = g
-                while len(self._mapped) > self.MAPPED_HANDLES:
+                while len(self._mapped) > self.HANDLES:
                     self._mapped.popitem(last=False)[1].close()
             self._mapped.move_to_end(key)
         else:
@@ -411,10 +411,10 @@ class HostSession:
             key = (n, nnz)
             g = self._graphs.get(key)
             if g is None:  # the handle only borrows the buffers; their contents change per run
-                for old in self._graphs.values():
-                    old.close()
-                self._graphs.clear()
                 g = self._graphs[key] = Graph(off_d, nb_d, check=False, stream=stream)
+                while len(self._graphs) > self.HANDLES:
+                    self._graphs.popitem(last=False)[1].close()
+            self._graphs.move_to_end(key)
         g.skipper(mate=mate_d, stream=stream, **kw)
         self.last_verdict = g.validate(mate_d, stream=stream) if check else None
         if mate_out is None:
