@@ -490,10 +490,12 @@ def run_served(args, skp, min_edges=None, max_edges=None, seconds=None, rate=Non
     out["served"] = {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
                      "gedges_s": entries / (end - t0) / 1e9, "launches": srv.ticks,
                      "mean_graphs_per_launch": statistics.mean(srv.tick_sizes), "invalid": bad,
-                     "how": "server.Server: admission by device-memory budget, H2D on a copy stream, "
-                            "one mm_skipper_multi launch per tick on two alternating compute streams, "
-                            "mm_validate_multi before completion, D2H on a second copy stream into "
-                            "a result buffer per pool graph (reused, as the serial run does)"}
+                     "how": "server.Server over the native mm_server: admission by device-memory "
+                            "budget; requests up to 1M entries read in place from pinned host memory, "
+                            "larger ones copied on a copy stream; one mm_skipper_multi launch per tick "
+                            "on two alternating compute streams, mm_validate_multi before completion, "
+                            "D2H on a second copy stream into a result buffer per pool graph (reused, "
+                            "as the serial run does)"}
     if not serial:
         return out
     # serial plain: one request at a time through the plain API, in arrival order

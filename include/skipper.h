@@ -53,7 +53,8 @@ typedef enum mm_status {
     MM_ERR_CUDA = 3,         /* a CUDA call failed (includes: no device) */
     MM_ERR_TIMEOUT = 4,      /* a wait on a reserved vertex exceeded spin_limit polls */
     MM_ERR_BAD_GRAPH = 5,    /* CSR check failed, or a neighbour id >= n was met */
-    MM_ERR_UNSUPPORTED = 6   /* option combination not supported */
+    MM_ERR_UNSUPPORTED = 6,  /* option combination not supported */
+    MM_PENDING = 7           /* mm_server_wait: the request has not completed yet */
 } mm_status;
 
 /* mm_create_csr flags */
@@ -406,6 +407,79 @@ mm_status mm_destroy(mm_graph *g);
 mm_status mm_skipper_static(uint64_t n, uint64_t nnz, const int64_t *d_offsets,
                             const uint32_t *d_nbrs, uint32_t *d_mate, const mm_options *o,
                             void *cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Serving: a continuous-batching server over graphs that live in host memory.
+ * No paper counterpart (the paper runs one graph at a time); it serves many
+ * independent requests through the multi-graph pass above.
+ *
+ * One worker thread admits requests in arrival order (no overtaking) while
+ * their device footprint fits memory_bytes and, whenever a compute slot is
+ * free, launches one mm_skipper_multi pass over everything admitted since the
+ * last launch, followed on the same stream by mm_validate_multi_async when
+ * validate is set.  With two slots a new batch is admitted and launched while
+ * the previous one runs.  A request with nnz <= in_place_max_nnz whose arrays
+ * the device can address (see MM_HOST_MAPPED) is read in place and its mate
+ * lives in a per-launch device arena; any other request is copied to its own
+ * stream-ordered device buffers.  Each mate array is copied back into the
+ * caller's h_mate_out.  The caller's arrays must stay valid and unchanged
+ * until the request's result has been collected.
+ * ------------------------------------------------------------------------ */
+typedef struct mm_server mm_server;
+
+typedef struct mm_server_config {
+    uint64_t memory_bytes;        /* device bytes resident requests may hold; 0 = the
+                                     free memory at creation minus reserve_bytes */
+    uint64_t reserve_bytes;       /* default 8 GiB */
+    uint64_t max_graphs_per_tick; /* graphs per launch, default 4096 */
+    uint64_t max_bytes_per_tick;  /* device bytes admitted per launch, default 32 GiB
+                                     (one larger request runs alone) */
+    uint64_t in_place_max_nnz;    /* largest request read in place, default 1 << 20 */
+    uint32_t validate;            /* 1 (default): check every result before completion */
+    uint32_t slots;               /* compute slots, 1 or 2 (default) */
+    mm_options opts;              /* options of the pass (status_bits, grain, serial, ...) */
+    uint64_t reserved[4];
+} mm_server_config;
+
+typedef struct mm_server_result {
+    mm_status status;    /* MM_OK; the pass's failure (MM_ERR_TIMEOUT, MM_ERR_BAD_GRAPH);
+                            MM_ERR_OOM when the request can never fit memory_bytes;
+                            MM_ERR_CUDA and the like when the server failed */
+    uint32_t in_place;   /* 1 when the request was read in place */
+    mm_verdict verdict;  /* the checker's verdict (validate set, status MM_OK) */
+    int64_t submit_ns;   /* CLOCK_MONOTONIC at submission */
+    int64_t done_ns;     /* CLOCK_MONOTONIC when the mate and the verdict were ready */
+} mm_server_result;
+
+/* Defaults (above) into *c.  MM_ERR_ARG for a null pointer. */
+mm_status mm_server_default_config(mm_server_config *c);
+/* Start a server on the current device.  MM_ERR_ARG (bad config), MM_ERR_CUDA,
+ * MM_ERR_OOM. */
+mm_status mm_server_create(const mm_server_config *c, mm_server **out);
+/* Queue one graph: host CSR (n vertices, nnz entries) and an n-entry host
+ * output h_mate_out (page-locked for an asynchronous copy).  Writes the
+ * request's ticket.  Thread-safe.  MM_ERR_ARG on a null array, n too large,
+ * or a closing server; the server's failure status once it has failed. */
+mm_status mm_server_submit(mm_server *s, uint64_t n, uint64_t nnz, const int64_t *h_offsets,
+                           const uint32_t *h_nbrs, uint32_t *h_mate_out, uint64_t *ticket);
+/* Collect a request's result, waiting up to timeout_s seconds (0 = poll).
+ * MM_OK with *out filled (each result is collected once), or MM_PENDING. */
+mm_status mm_server_wait(mm_server *s, uint64_t ticket, double timeout_s, mm_server_result *out);
+/* Launches so far, graphs launched, device bytes held by admitted requests
+ * (any pointer may be NULL). */
+mm_status mm_server_stats(mm_server *s, uint64_t *launches, uint64_t *graphs,
+                          uint64_t *device_bytes_held);
+/* Drain every queued request, then release the server.  Results not yet
+ * collected are dropped.  Returns the server's failure status, if any. */
+mm_status mm_server_destroy(mm_server *s);
+/* Admission arithmetic, exposed for tests: the device bytes a request holds
+ * while resident (in place: mate and scratch; copied: plus its CSR), and how
+ * many of the pending sizes (arrival order) fit: stops at the first that does
+ * not (no overtaking) or at max_graphs. */
+mm_status mm_server_device_bytes(uint64_t n, uint64_t nnz, uint32_t in_place, uint64_t *out);
+mm_status mm_server_plan_admission(const uint64_t *sizes, uint64_t count, uint64_t used,
+                                   uint64_t budget, uint64_t max_graphs, uint64_t *k_out,
+                                   uint64_t *bytes_out);
 
 #ifdef __cplusplus
 }

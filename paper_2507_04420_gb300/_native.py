@@ -19,7 +19,7 @@ CSRC = os.path.join(_PKG, "csrc")
 INCLUDE = os.path.join(_ROOT, "include")
 LIB_DIR = os.path.join(_PKG, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libskipper.so")
-SOURCES = ["sweep.cu", "check.cu", "api.cu", "noalloc.cu", "multi.cu", "coo.cu"]
+SOURCES = ["sweep.cu", "check.cu", "api.cu", "noalloc.cu", "multi.cu", "coo.cu", "server.cu"]
 HEADERS = ["state.cuh", "internal.h", "walk.cuh", "checkwalk.cuh"]
 
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -113,25 +113,6 @@ class GraphDesc(ctypes.Structure):
     ]
 
 
-class Stats(ctypes.Structure):
-    _fields_ = [
-        ("entries_read", ctypes.c_uint64),
-        ("windows", ctypes.c_uint64),
-        ("chunks", ctypes.c_uint64),
-        ("attempts", ctypes.c_uint64),
-        ("matches", ctypes.c_uint64),
-        ("conflicts", ctypes.c_uint64),
-        ("conflicted_entries", ctypes.c_uint64),
-        ("max_conflicts", ctypes.c_uint64),
-        ("hist", ctypes.c_uint64 * 10),
-    ]
-
-    def as_dict(self):
-        d = {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "hist"}
-        d["hist"] = [int(x) for x in self.hist]
-        return d
-
-
 class Verdict(ctypes.Structure):
     _fields_ = [
         ("flags", ctypes.c_uint32),
@@ -151,6 +132,49 @@ class Verdict(ctypes.Structure):
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k in self.FIELDS}
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [
+        ("memory_bytes", ctypes.c_uint64),
+        ("reserve_bytes", ctypes.c_uint64),
+        ("max_graphs_per_tick", ctypes.c_uint64),
+        ("max_bytes_per_tick", ctypes.c_uint64),
+        ("in_place_max_nnz", ctypes.c_uint64),
+        ("validate", ctypes.c_uint32),
+        ("slots", ctypes.c_uint32),
+        ("opts", Options),
+        ("reserved", ctypes.c_uint64 * 4),
+    ]
+
+
+class ServerResult(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("in_place", ctypes.c_uint32),
+        ("verdict", Verdict),
+        ("submit_ns", ctypes.c_int64),
+        ("done_ns", ctypes.c_int64),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("entries_read", ctypes.c_uint64),
+        ("windows", ctypes.c_uint64),
+        ("chunks", ctypes.c_uint64),
+        ("attempts", ctypes.c_uint64),
+        ("matches", ctypes.c_uint64),
+        ("conflicts", ctypes.c_uint64),
+        ("conflicted_entries", ctypes.c_uint64),
+        ("max_conflicts", ctypes.c_uint64),
+        ("hist", ctypes.c_uint64 * 10),
+    ]
+
+    def as_dict(self):
+        d = {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "hist"}
+        d["hist"] = [int(x) for x in self.hist]
+        return d
 
 
 # exported symbols, in header order: (name, restype, argtypes)
@@ -179,10 +203,19 @@ SYMBOLS = [
     ("mm_multi_destroy", _I, [_P]),
     ("mm_destroy", _I, [_P]),
     ("mm_skipper_static", _I, [_U64, _U64, _P, _P, _P, ctypes.POINTER(Options), _P]),
+    ("mm_server_default_config", _I, [ctypes.POINTER(ServerConfig)]),
+    ("mm_server_create", _I, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]),
+    ("mm_server_submit", _I, [_P, _U64, _U64, _P, _P, _P, ctypes.POINTER(_U64)]),
+    ("mm_server_wait", _I, [_P, _U64, ctypes.c_double, ctypes.POINTER(ServerResult)]),
+    ("mm_server_stats", _I, [_P, ctypes.POINTER(_U64), ctypes.POINTER(_U64), ctypes.POINTER(_U64)]),
+    ("mm_server_destroy", _I, [_P]),
+    ("mm_server_device_bytes", _I, [_U64, _U64, _U32, ctypes.POINTER(_U64)]),
+    ("mm_server_plan_admission", _I, [ctypes.POINTER(_U64), _U64, _U64, _U64, _U64, ctypes.POINTER(_U64),
+                                      ctypes.POINTER(_U64)]),
 ]
 
 STATUS = {0: "MM_OK", 1: "MM_ERR_ARG", 2: "MM_ERR_OOM", 3: "MM_ERR_CUDA", 4: "MM_ERR_TIMEOUT",
-          5: "MM_ERR_BAD_GRAPH", 6: "MM_ERR_UNSUPPORTED"}
+          5: "MM_ERR_BAD_GRAPH", 6: "MM_ERR_UNSUPPORTED", 7: "MM_PENDING"}
 
 _lock = threading.Lock()
 _lib = None

@@ -1,90 +1,88 @@
-"""Continuous-batching Skipper server on one GPU.
+"""Continuous-batching Skipper server on one GPU (binding of the native server).
 
-Requests (graphs in host memory) arrive at any time.  A worker thread admits
-them in arrival order while their device footprint fits the memory budget and
-whenever a compute slot is free launches one multi-graph pass
-(mm_skipper_multi) over every request admitted since the last launch.  Two
-compute slots alternate, so a new batch is admitted and launched while the
-previous one is still on the GPU.  Each result is checked by the exact device
-checker (mm_validate_multi) before its request completes; its mate array is
-copied back on a second copy stream.
+The serving loop runs in the library (``mm_server_*`` in ``include/skipper.h``,
+``csrc/server.cu``): one native worker thread admits requests in arrival
+order while their device footprint fits the memory budget and, whenever a
+compute slot is free, launches one multi-graph pass (mm_skipper_multi) over
+every request admitted since the last launch, then the exact device checker
+(mm_validate_multi) on the same stream.  Two compute slots alternate, so a new
+batch is admitted and launched while the previous one is still on the GPU.
 
-A request reaches the GPU one of two ways.  Small requests in page-locked
-memory (up to in_place_max_nnz entries) are read in place: the kernels read
-their CSR through the host link (their device addresses come from
-mm_host_device_address on the client thread), and their mate arrays share one
-device arena per launch -- no device allocation and no host->device copy per
-request.  Larger ones are copied to their own device buffers on a copy stream
-(their checker reads every entry, which one bulk copy serves best); the CSR and
-the state stay resident until the request completes.
+A request reaches the GPU one of two ways.  Small requests (up to
+in_place_max_nnz entries) whose host arrays the device can address are read
+in place through the host link, their mate arrays sharing one device arena per
+launch; larger ones are copied to their own device buffers.  Each mate array
+is copied back into the request's host buffer.
 
-Latency of a request = completion (mate in host memory, verdict known) minus
-submission.
+This module only marshals tensors: Server.submit hands the host arrays to the
+native server and Request.wait collects the result (the wait runs in C, without
+the interpreter lock).  Latency of a request = completion (mate in host
+memory, verdict known) minus submission, both on the monotonic clock that
+time.perf_counter() reads.
 """
 from __future__ import annotations
 
-import collections
-import queue
+import ctypes
 import threading
 import time
-from typing import List, Optional, Sequence, Tuple
+from typing import Dict, List, Optional, Sequence, Tuple
 
 import torch
 
-from . import GraphDesc, Multi, SkipperError, device_address, options
+from . import SkipperError, lib, options
+from ._native import ServerConfig, ServerResult, Verdict
 
 __all__ = ["Request", "Server", "device_bytes", "plan_admission"]
 
+MM_OK, MM_ERR_OOM, MM_PENDING = 0, 2, 7
+
+
+def _ok(code: int, where: str):
+    if code != MM_OK:
+        raise SkipperError(code, where)
+
 
 def device_bytes(n: int, nnz: int, in_place: bool = False) -> int:
-    """Device memory a request holds while resident: offsets and neighbour ids
-    (not when read in place), mate, plus its share of the launch scratch
-    (packed states, partition and unit tables, the checker's marks), rounded
-    up to 512-byte granules."""
-    r = lambda b: (b + 511) // 512 * 512
-    scratch = (n // 4 + 8) + n + 24 * ((n + nnz) // 1024 + 2)
-    csr = 0 if in_place else r(8 * (n + 1)) + r(4 * max(nnz, 1))
-    return csr + r(4 * max(n, 1)) + r(scratch)
+    """Device memory a request holds while resident (mm_server_device_bytes):
+    its CSR unless read in place, its mate, and its share of the launch scratch
+    (packed states, partition and unit tables, the checker's marks)."""
+    out = ctypes.c_uint64()
+    _ok(lib.mm_server_device_bytes(n, nnz, 1 if in_place else 0, ctypes.byref(out)), "mm_server_device_bytes")
+    return int(out.value)
 
 
 def plan_admission(sizes: Sequence[int], used: int, budget: int, max_graphs: int) -> Tuple[int, int]:
-    """How many of the pending requests (sizes in bytes, arrival order) to admit.
-
-    Admission is in arrival order and stops at the first request that does not
-    fit (no overtaking, so no request starves).  Returns (count, bytes)."""
-    k = 0
-    add = 0
-    for s in sizes:
-        if k >= max_graphs or used + add + s > budget:
-            break
-        add += s
-        k += 1
-    return k, add
+    """How many of the pending requests (sizes in bytes, arrival order) to admit
+    (mm_server_plan_admission): in arrival order, stopping at the first that
+    does not fit (no overtaking, so no request starves).  Returns (count, bytes)."""
+    arr = (ctypes.c_uint64 * max(1, len(sizes)))(*sizes)
+    k, add = ctypes.c_uint64(), ctypes.c_uint64()
+    _ok(lib.mm_server_plan_admission(arr, len(sizes), used, budget, max_graphs, ctypes.byref(k),
+                                     ctypes.byref(add)), "mm_server_plan_admission")
+    return int(k.value), int(add.value)
 
 
 class Request:
     __slots__ = ("rid", "offsets", "nbrs", "n", "nnz", "arrival", "done_t", "mate", "verdict",
-                 "error", "in_place", "_event", "_dev", "_addr", "_mate_d", "_bytes", "tick")
+                 "error", "in_place", "_server", "_lock")
 
-    def __init__(self, rid: int, offsets: torch.Tensor, nbrs: torch.Tensor, in_place: bool = False):
-        self.rid = rid
-        self.offsets, self.nbrs = offsets, nbrs
+    def __init__(self, server: "Server", offsets: torch.Tensor, nbrs: torch.Tensor, mate: torch.Tensor):
+        self.rid = 0
+        self.offsets, self.nbrs, self.mate = offsets, nbrs, mate   # kept alive until collected
         self.n, self.nnz = offsets.numel() - 1, nbrs.numel()
         self.arrival = time.perf_counter()
         self.done_t = None
-        self.mate = None
         self.verdict = None
         self.error = None
-        self.in_place = in_place
-        self._event = threading.Event()
-        self._dev = None
-        self._addr = None      # (offsets, nbrs) device addresses when read in place
-        self._mate_d = None    # device mate (a slice of the launch's arena when read in place)
-        self._bytes = device_bytes(self.n, self.nnz, in_place)
-        self.tick = None
+        self.in_place = None
+        self._server = server
+        self._lock = threading.Lock()
 
     def wait(self, timeout: Optional[float] = None) -> bool:
-        return self._event.wait(timeout)
+        """Wait for the result (True once it is in: mate, verdict, error set)."""
+        if self.done_t is not None:
+            return True
+        return self._server._collect(self, 1e9 if timeout is None else timeout)
 
     @property
     def latency(self) -> Optional[float]:
@@ -97,210 +95,122 @@ class Server:
                  status_bits: int = 32, grain: int = 2048, serial: bool = False,
                  validate: bool = True, slots: int = 2, in_place_max_nnz: int = 1 << 20):
         self.dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-        free, _ = torch.cuda.mem_get_info(self.dev)
-        self.budget = memory_bytes if memory_bytes is not None else max(0, free - reserve_bytes)
-        self.max_graphs = max_graphs_per_tick
-        self.max_tick_bytes = max_bytes_per_tick
+        cfg = ServerConfig()
+        _ok(lib.mm_server_default_config(ctypes.byref(cfg)), "mm_server_default_config")
+        cfg.memory_bytes = 0 if memory_bytes is None else int(memory_bytes)
+        cfg.reserve_bytes = reserve_bytes
+        cfg.max_graphs_per_tick = max_graphs_per_tick
+        cfg.max_bytes_per_tick = max_bytes_per_tick
+        cfg.in_place_max_nnz = in_place_max_nnz
+        cfg.validate = 1 if validate else 0
+        cfg.slots = slots
+        cfg.opts = options(status_bits=status_bits, grain=grain, serial=int(serial), nosync=1)
         self.validate = validate
-        self.in_place_max_nnz = in_place_max_nnz
-        self.opts = options(status_bits=status_bits, grain=grain, serial=int(serial), nosync=1)
-        self.h2d = torch.cuda.Stream(self.dev)
-        self.d2h = torch.cuda.Stream(self.dev)
-        self.slots = [(torch.cuda.Stream(self.dev), Multi()) for _ in range(slots)]
-        self._next_slot = 0
-        self._inbox: "queue.Queue[Request]" = queue.Queue()
-        self._rid = 0
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.dev):
+            _ok(lib.mm_server_create(ctypes.byref(cfg), ctypes.byref(h)), "mm_server_create")
+        self._h = h
+        if memory_bytes is None:
+            free, _ = torch.cuda.mem_get_info(self.dev)
+            self.budget = max(0, free - reserve_bytes)
+        else:
+            self.budget = int(memory_bytes)
+        self._live: Dict[int, Request] = {}
         self._lock = threading.Lock()
-        self._closing = False
-        self.used = 0
         self.ticks = 0
-        self.tick_sizes: List[int] = []
+        self.graphs_launched = 0
         self.error: Optional[BaseException] = None
-        self._thread = threading.Thread(target=self._run, name="skipper-server", daemon=True)
-        self._thread.start()
 
     # -- client side ------------------------------------------------------------
     def submit(self, offsets: torch.Tensor, nbrs: torch.Tensor,
                mate_out: Optional[torch.Tensor] = None) -> Request:
-        """Queue one graph (host CSR; pinned memory makes the copy asynchronous).
+        """Queue one graph (host CSR; page-locked memory makes the copies
+        asynchronous and small requests eligible for reading in place).
 
-        mate_out: optional host int32 tensor of n entries (pinned for an
+        mate_out: optional host int32 tensor of n entries (page-locked for an
         asynchronous copy) that receives the result; a client that recycles
         its result buffers keeps pinned allocations out of the serving loop.
         Without it the server allocates one."""
         if offsets.is_cuda or nbrs.is_cuda:
             raise ValueError("submit host tensors")
-        if mate_out is not None and (mate_out.is_cuda or mate_out.numel() != offsets.numel() - 1
-                                     or mate_out.dtype != torch.int32):
-            raise ValueError("mate_out must be a host int32 tensor of n entries")
+        if offsets.dtype != torch.int64 or nbrs.dtype != torch.int32:
+            raise TypeError("offsets must be int64 and nbrs int32 (uint32 bits)")
+        if not (offsets.is_contiguous() and nbrs.is_contiguous()):
+            raise ValueError("offsets and nbrs must be contiguous")
+        n = offsets.numel() - 1
+        if mate_out is None:
+            mate_out = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        elif (mate_out.is_cuda or mate_out.numel() != n or mate_out.dtype != torch.int32
+              or not mate_out.is_contiguous()):
+            raise ValueError("mate_out must be a contiguous host int32 tensor of n entries")
+        req = Request(self, offsets, nbrs, mate_out)
+        ticket = ctypes.c_uint64()
+        rc = lib.mm_server_submit(self._h, n, nbrs.numel(), ctypes.c_void_p(offsets.data_ptr()),
+                                  ctypes.c_void_p(nbrs.data_ptr()) if nbrs.numel() else None,
+                                  ctypes.c_void_p(mate_out.data_ptr()) if n else None, ctypes.byref(ticket))
+        if rc != MM_OK:
+            req.error = SkipperError(rc, "mm_server_submit")
+            req.done_t = time.perf_counter()
+            return req
+        req.rid = int(ticket.value)
         with self._lock:
-            rid = self._rid
-            self._rid += 1
-        nnz = nbrs.numel()
-        in_place = (nnz <= self.in_place_max_nnz and offsets.is_pinned() and (nnz == 0 or nbrs.is_pinned())
-                    and offsets.dtype == torch.int64 and nbrs.dtype in (torch.int32,)
-                    and offsets.is_contiguous() and nbrs.is_contiguous())
-        req = Request(rid, offsets, nbrs, in_place)
-        if in_place:   # resolved here, on the client thread
-            req._addr = (device_address(offsets), device_address(nbrs) if nnz else 0)
-        req.mate = mate_out
-        if self.error is not None:
-            req.error = self.error
-            req.done_t = time.perf_counter()
-            req._event.set()
-            return req
-        if req._bytes > self.budget:
-            req.error = MemoryError(f"request needs {req._bytes} device bytes, budget {self.budget}")
-            req.done_t = time.perf_counter()
-            req._event.set()
-            return req
-        self._inbox.put(req)
+            self._live[req.rid] = req
         return req
 
-    def close(self, timeout: float = 600.0):
-        self._closing = True
-        self._thread.join(timeout)
-        for _, m in self.slots:
-            m.close()
-        if self.error is not None:
-            raise self.error
-
-    # -- worker -------------------------------------------------------------------
-    def _admit(self, req: Request):
-        if req.in_place:       # its mate is carved from the launch's arena
-            return
-        with torch.cuda.stream(self.h2d):
-            off = torch.empty(req.n + 1, dtype=torch.int64, device=self.dev)
-            nb = torch.empty(max(req.nnz, 1), dtype=torch.int32, device=self.dev)[: req.nnz]
-            mate = torch.empty(req.n, dtype=torch.int32, device=self.dev)
-            off.copy_(req.offsets, non_blocking=True)
-            if req.nnz:
-                nb.copy_(req.nbrs, non_blocking=True)
-        req._dev = (off, nb, mate)
-        req._mate_d = mate
-
-    def _launch(self, batch: List[Request]):
-        stream, multi = self.slots[self._next_slot]
-        slot = self._next_slot
-        self._next_slot = (self._next_slot + 1) % len(self.slots)
-        copied = torch.cuda.Event()
-        copied.record(self.h2d)
-        stream.wait_event(copied)
-        arena = None
-        total = sum(r.n for r in batch if r.in_place)
-        if total:  # one device allocation for the mates of all in-place requests
-            with torch.cuda.stream(stream):
-                arena = torch.empty(total, dtype=torch.int32, device=self.dev)
-            at = 0
-            for r in batch:
-                if r.in_place:
-                    r._mate_d = arena[at:at + r.n]
-                    at += r.n
-        arr = (GraphDesc * max(1, len(batch)))()
-        for i, r in enumerate(batch):
-            d = arr[i]
-            d.n, d.nnz = r.n, r.nnz
-            if r.in_place:
-                d.offsets, d.nbrs = r._addr[0], (r._addr[1] or None)
+    def _collect(self, req: Request, timeout: float) -> bool:
+        with req._lock:
+            if req.done_t is not None:
+                return True
+            res = ServerResult()
+            rc = lib.mm_server_wait(self._h, req.rid, float(timeout), ctypes.byref(res))
+            if rc == MM_PENDING:
+                return False
+            _ok(rc, "mm_server_wait")
+            req.in_place = bool(res.in_place)
+            req.arrival = res.submit_ns * 1e-9
+            if res.status == MM_OK:
+                if self.validate:
+                    v = Verdict()
+                    ctypes.memmove(ctypes.byref(v), ctypes.byref(res.verdict), ctypes.sizeof(Verdict))
+                    req.verdict = v
+            elif res.status == MM_ERR_OOM:
+                req.error = MemoryError(f"request needs {device_bytes(req.n, req.nnz, req.in_place)} "
+                                        f"device bytes, budget {self.budget}")
             else:
-                d.offsets, d.nbrs = r._dev[0].data_ptr(), (r._dev[1].data_ptr() if r.nnz else None)
-            d.mate = r._mate_d.data_ptr() if r.n else None
-        multi.run_descs(arr, len(batch), stream=stream, opts=self.opts)
-        swept = torch.cuda.Event()
-        swept.record(stream)
-        if self.validate:  # the checker runs behind the pass, on the same stream
-            multi.validate_async_descs(arr, len(batch), stream=stream)
-        checked = torch.cuda.Event()
-        checked.record(stream)
-        for r in batch:  # the device tensors were made on the copy stream; they are used here too
-            if r._dev is not None:
-                for t in r._dev:
-                    t.record_stream(stream)
-        self.d2h.wait_event(swept)
-        with torch.cuda.stream(self.d2h):
-            for r in batch:
-                if r.mate is None:
-                    r.mate = torch.empty(r.n, dtype=torch.int32, pin_memory=True)
-                r.mate.copy_(r._mate_d, non_blocking=True)
-            if arena is not None:
-                arena.record_stream(self.d2h)
-            for r in batch:
-                if r._dev is not None:
-                    r._dev[2].record_stream(self.d2h)
-        back = torch.cuda.Event()
-        back.record(self.d2h)
-        self.ticks += 1
-        self.tick_sizes.append(len(batch))
-        return (slot, batch, back, checked)
-
-    def _complete(self, tick) -> bool:
-        slot, batch, back, checked = tick
-        if not (back.query() and checked.query()):
-            return False
-        stream, multi = self.slots[slot]
-        err = None
-        try:
-            multi.sync(stream)  # the pass's own status (timeouts, bad ids)
-        except SkipperError as e:
-            err = e
-        verdicts = multi.verdicts(len(batch)) if (self.validate and err is None) else None
-        now = time.perf_counter()
-        for i, r in enumerate(batch):
-            r.verdict = None if verdicts is None else verdicts[i]
-            r.error = err
-            r.done_t = now
-            r._dev = None
-            r._mate_d = None
-            self.used -= r._bytes
-            r._event.set()
+                req.error = SkipperError(res.status, "server request")
+            req.done_t = res.done_ns * 1e-9
+        with self._lock:
+            self._live.pop(req.rid, None)
         return True
 
-    def _run(self):
-        pending: "collections.deque[Request]" = collections.deque()
-        staged: List[Request] = []
-        inflight: "collections.deque" = collections.deque()
-        torch.cuda.set_device(self.dev)
+    def stats(self) -> Tuple[int, int, int]:
+        """(launches, graphs launched, device bytes held by admitted requests)."""
+        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _ok(lib.mm_server_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "mm_server_stats")
+        return int(a.value), int(b.value), int(c.value)
+
+    @property
+    def tick_sizes(self) -> List[float]:
+        """Mean graphs per launch, as a one-element list (the native server keeps totals)."""
+        return [self.graphs_launched / self.ticks] if self.ticks else [0.0]
+
+    def close(self, timeout: float = 600.0):
+        """Collect every outstanding result, then stop the native server."""
+        if not getattr(self, "_h", None):
+            return
+        with self._lock:
+            live = list(self._live.values())
+        for r in live:
+            r.wait(timeout)
+        self.ticks, self.graphs_launched, _ = self.stats()
+        rc = lib.mm_server_destroy(self._h)
+        self._h = None
+        if rc != MM_OK:
+            self.error = SkipperError(rc, "mm_server_destroy")
+            raise self.error
+
+    def __del__(self):
         try:
-            while True:
-                busy = False
-                while True:
-                    try:
-                        pending.append(self._inbox.get_nowait())
-                    except queue.Empty:
-                        break
-                while inflight and self._complete(inflight[0]):
-                    inflight.popleft()
-                    busy = True
-                staged_bytes = sum(r._bytes for r in staged)
-                room = min(self.budget, self.used + self.max_tick_bytes - staged_bytes)
-                k, add = plan_admission([r._bytes for r in pending], self.used, room,
-                                        self.max_graphs - len(staged))
-                if k == 0 and not staged and not inflight and pending and pending[0]._bytes > self.max_tick_bytes:
-                    k, add = 1, pending[0]._bytes  # one request larger than a tick runs alone
-                for _ in range(k):
-                    r = pending.popleft()
-                    self._admit(r)
-                    staged.append(r)
-                    busy = True
-                self.used += add
-                if staged and len(inflight) < len(self.slots):
-                    inflight.append(self._launch(staged))
-                    staged = []
-                    busy = True
-                if self._closing and not pending and not staged and not inflight and self._inbox.empty():
-                    return
-                if not busy:
-                    time.sleep(50e-6)
-        except BaseException as e:  # surface worker failures to close() and to every waiter
-            self.error = e
-            self._closing = True
-            left = list(pending) + staged + [r for t in inflight for r in t[1]]
-            while True:
-                try:
-                    left.append(self._inbox.get_nowait())
-                except queue.Empty:
-                    break
-            for r in left:
-                r.error = e
-                r.done_t = time.perf_counter()
-                r._event.set()
+            self.close()
+        except Exception:
+            pass

@@ -51,6 +51,10 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(mm_options), offsetof(mm_options, spin_limit),
          offsetof(mm_options, poison_vertex), sizeof(mm_verdict),
          offsetof(mm_verdict, first_uncovered), sizeof(mm_timing), offsetof(mm_timing, units));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", offsetof(mm_options, symmetric), sizeof(mm_server_config),
+         offsetof(mm_server_config, opts), offsetof(mm_server_config, reserved),
+         sizeof(mm_server_result), offsetof(mm_server_result, verdict),
+         offsetof(mm_server_result, done_ns), sizeof(mm_graph_desc));
   return 0;
 }
 """
@@ -61,8 +65,11 @@ int main(void) {
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         vals = [int(x) for x in subprocess.check_output([exe]).split()]
     O, V, T = native.Options, native.Verdict, native.Timing
+    C, R, G = native.ServerConfig, native.ServerResult, native.GraphDesc
     assert vals == [ctypes.sizeof(O), O.spin_limit.offset, O.poison_vertex.offset,
-                    ctypes.sizeof(V), V.first_uncovered.offset, ctypes.sizeof(T), T.units.offset]
+                    ctypes.sizeof(V), V.first_uncovered.offset, ctypes.sizeof(T), T.units.offset,
+                    O.symmetric.offset, ctypes.sizeof(C), C.opts.offset, C.reserved.offset,
+                    ctypes.sizeof(R), R.verdict.offset, R.done_ns.offset, ctypes.sizeof(G)]
 
 
 def test_default_options_and_argument_errors(native):

@@ -143,3 +143,34 @@ def test_server_rejects_what_can_never_fit(skp):
     vr = oracle.check(g.offsets.numpy(), g.nbrs.numpy(), r3.mate.numpy().view(np.uint32))
     assert vr.flags == 0 and vr.as_dict() == r3.verdict.as_dict()
     srv.close()
+
+
+def test_server_many_client_threads(skp, graphs):
+    """Four client threads submit at once; every result matches the graph's
+    serial result alone (SGMM order), whichever way the request went in."""
+    from paper_2507_04420_gb300.server import Server
+    alone = {}
+    for i, g in enumerate(graphs):
+        ref, _ = oracle.sgmm(g.offsets.numpy(), g.nbrs.numpy())
+        alone[i] = ref
+    pinned = [_pinned(g) for g in graphs]
+    srv = Server(serial=True, status_bits=8, in_place_max_nnz=20000)
+    out = [[] for _ in range(4)]
+
+    def client(k):
+        for rep in range(3):
+            for i in range(k, len(graphs), 2):
+                out[k].append((i, srv.submit(*pinned[i])))
+
+    ts = [threading.Thread(target=client, args=(k,)) for k in range(4)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    for lst in out:
+        for i, r in lst:
+            assert r.wait(120) and r.error is None
+            assert np.array_equal(r.mate.numpy().view(np.uint32), alone[i])
+            assert r.verdict.flags == 0 and r.latency >= 0
+    srv.close()
+    assert srv.ticks >= 1 and srv.graphs_launched == sum(len(x) for x in out)
