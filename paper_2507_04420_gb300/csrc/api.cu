@@ -774,15 +774,15 @@ mm_status mm_validate(mm_graph* g, const uint32_t* d_mate, const uint32_t* d_pai
   if (d_pairs && count && !g->seen_bits)
     CUDA_TRY(cudaMalloc(&g->seen_bits, ((g->n + 31) / 32 + 1) * sizeof(uint32_t)));
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  if (!g->found) CUDA_TRY(cudaMalloc(&g->found, g->n + 16));
   if (g->coo) {
+    if (!g->found) CUDA_TRY(cudaMalloc(&g->found, g->n + 16));
     CheckScratch cs{counters_ptr(g), g->seen_bits, g->tile_counts, g->tile_cap, g->found, nullptr};
     CUDA_TRY(launch_validate_coo(g->n, g->nnz, g->src, g->dst, d_mate, d_pairs, d_pairs ? count : 0, cs,
                                  prepare_grid(g), s));
   } else {
     if (!g->check_part)
       CUDA_TRY(cudaMalloc(&g->check_part, ((g->n + g->nnz) / kCheckGrain + 2) * 2 * sizeof(int64_t)));
-    CheckScratch cs{counters_ptr(g), g->seen_bits, g->tile_counts, g->tile_cap, g->found, g->check_part};
+    CheckScratch cs{counters_ptr(g), g->seen_bits, g->tile_counts, g->tile_cap, nullptr, g->check_part};
     CUDA_TRY(launch_validate(g->n, g->nnz, g->offsets, g->nbrs, d_mate, d_pairs, d_pairs ? count : 0, cs,
                              prepare_grid(g), s));
   }

@@ -76,12 +76,10 @@ __global__ void check_partition_kernel(uint64_t n, uint64_t nnz, const int64_t* 
   }
 }
 
-// edge pass (checkwalk.cuh): uncovered entries, and found[x] for every x whose
-// partner appears in row x
+// edge pass (checkwalk.cuh): uncovered entries, in the rows of unmatched vertices
 __global__ void validate_edges_kernel(uint64_t n, uint64_t nnz, const int64_t* __restrict__ offsets,
                                       const uint32_t* __restrict__ nbrs,
                                       const uint32_t* __restrict__ mate,
-                                      unsigned char* __restrict__ found,
                                       const int64_t* __restrict__ part, uint64_t units,
                                       unsigned long long* __restrict__ c) {
   const unsigned lane = threadIdx.x & 31u;
@@ -90,7 +88,7 @@ __global__ void validate_edges_kernel(uint64_t n, uint64_t nnz, const int64_t* _
   unsigned long long unc = 0, first = ~0ull;
   for (uint64_t u = warp; u < units; u += nwarps) {
     const int64_t e0 = part[2 * u + 1], e1 = part[2 * u + 3];
-    if (e0 < e1) check_unit(offsets, nbrs, n, nnz, mate, found, part[2 * u], e0, e1, lane, unc, first);
+    if (e0 < e1) check_unit(offsets, nbrs, n, nnz, mate, part[2 * u], e0, e1, lane, unc, first);
   }
   unc = warp_sum64(unc);
   first = warp_min64(first);
@@ -134,8 +132,27 @@ __global__ void validate_coo_edges_kernel(uint64_t n, uint64_t m, const uint32_t
   }
 }
 
-// vertex pass: range / symmetry of each named partner, and its existence
-// from the edge pass's found marks
+// existence pass (checkwalk.cuh): each named partner must share an edge with
+// its vertex; one warp per 32 consecutive vertices
+__global__ void validate_exist_kernel(uint64_t n, const int64_t* __restrict__ offsets,
+                                      const uint32_t* __restrict__ nbrs,
+                                      const uint32_t* __restrict__ mate,
+                                      unsigned long long* __restrict__ c) {
+  const unsigned lane = threadIdx.x & 31u;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long nonedge = 0, first = ~0ull;
+  for (uint64_t v0 = warp * 32; v0 < n; v0 += nwarps * 32)
+    check_pairs32(offsets, nbrs, n, mate, v0, lane, nonedge, first);
+  if (lane == 0) {
+    if (nonedge) atomicAdd(c + C_NONEDGE, nonedge);
+    if (first != ~0ull) atomicMin(c + C_FIRST_BAD, first);
+  }
+}
+
+// vertex pass: range / symmetry of each named partner; with `found` (edge
+// lists: the edge pass marks every vertex whose partner edge it met) also its
+// existence -- a CSR's existence pass is validate_exist_kernel
 __global__ void validate_vertex_kernel(uint64_t n, const uint32_t* __restrict__ mate,
                                        const unsigned char* __restrict__ found,
                                        unsigned long long* __restrict__ c) {
@@ -158,7 +175,7 @@ __global__ void validate_vertex_kernel(uint64_t n, const uint32_t* __restrict__ 
           } else if (v < m) {
             pair = 1;
           }
-          if (!found[v] && !found[m]) {  // the edge may be stored for either endpoint
+          if (found && !found[v] && !found[m]) {  // the edge may be listed either way
             nonedge = 1;
             bad = true;
           }
@@ -313,11 +330,11 @@ cudaError_t launch_validate(uint64_t n, uint64_t nnz, const int64_t* offsets, co
   zero_u64_kernel<<<1, 32, 0, s>>>(cs.counters + C_FIRST_BAD, 2, ~0ull);
   if (pairs && count) zero_u32_kernel<<<grid, 256, 0, s>>>(cs.seen_bits, (n + 31) / 32);
   if (n) {
-    zero_u32_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<uint32_t*>(cs.found), (n + 3) / 4);
     const uint64_t units = (n + nnz + kCheckGrain - 1) / kCheckGrain;
     check_partition_kernel<<<grid, 256, 0, s>>>(n, nnz, offsets, kCheckGrain, units, cs.part);
-    if (nnz) validate_edges_kernel<<<grid, 256, 0, s>>>(n, nnz, offsets, nbrs, mate, cs.found, cs.part, units, cs.counters);
-    validate_vertex_kernel<<<grid, 256, 0, s>>>(n, mate, cs.found, cs.counters);
+    if (nnz) validate_edges_kernel<<<grid, 256, 0, s>>>(n, nnz, offsets, nbrs, mate, cs.part, units, cs.counters);
+    validate_exist_kernel<<<grid, 256, 0, s>>>(n, offsets, nbrs, mate, cs.counters);
+    validate_vertex_kernel<<<grid, 256, 0, s>>>(n, mate, nullptr, cs.counters);
   }
   if (pairs && count) validate_pairs_kernel<<<grid, 256, 0, s>>>(n, mate, pairs, count, cs.seen_bits, cs.counters);
   return cudaGetLastError();

@@ -43,7 +43,7 @@ struct CheckScratch {
   uint32_t* seen_bits;           // ceil(n/32) words
   uint64_t* block_counts;        // compaction: one count per tile of vertices
   uint64_t block_cap;
-  unsigned char* found;          // checker: n bytes (+3), partner edge seen in the row
+  unsigned char* found;          // edge-list checker: n bytes (+3), partner edge met in the list
   int64_t* part;                 // checker: merge-path table, (n+nnz)/kCheckGrain + 1 pairs
 };
 constexpr uint64_t kCheckGrain = 4096;  // rows + entries per checker work unit

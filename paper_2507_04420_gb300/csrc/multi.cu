@@ -42,7 +42,6 @@ struct MultiParams {
   uint32_t* err;
   uint64_t spin_limit;
   unsigned long long* counters;  // checker: 9 per graph
-  unsigned char* found;          // checker: one byte per vertex of every graph
 };
 
 // last g with base[g] <= x, base[0] = 0, base ascending, g < G
@@ -165,13 +164,6 @@ __global__ void multi_partition_kernel(MultiParams M) {
   }
 }
 
-__global__ void multi_clear_found_kernel(MultiParams M) {
-  const uint64_t V = M.vbase[M.num_graphs];
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V;
-       i += (uint64_t)gridDim.x * blockDim.x)
-    M.found[i] = 0;
-}
-
 // the checker's edge pass (checkwalk.cuh) over the units of every graph
 __global__ void multi_validate_edges_kernel(MultiParams M) {
   const unsigned lane = threadIdx.x & 31u;
@@ -184,8 +176,7 @@ __global__ void multi_validate_edges_kernel(MultiParams M) {
     const int64_t e1 = (u + 1 < M.units && M.gid[u + 1] == g) ? M.part[2 * u + 3] : (int64_t)d.nnz;
     if (e0 >= e1) continue;
     unsigned long long unc = 0, first = ~0ull;
-    check_unit(d.offsets, d.nbrs, d.n, d.nnz, d.mate, M.found + M.vbase[g], M.part[2 * u], e0, e1,
-               lane, unc, first);
+    check_unit(d.offsets, d.nbrs, d.n, d.nnz, d.mate, M.part[2 * u], e0, e1, lane, unc, first);
     unc = warp_sum64(unc);
     first = warp_min64(first);
     if (lane == 0) {
@@ -196,7 +187,52 @@ __global__ void multi_validate_edges_kernel(MultiParams M) {
   }
 }
 
-// the checker's vertex pass on every vertex of every graph, counters kept per graph
+// the checker's existence pass (checkwalk.cuh) over every vertex of every
+// graph: one warp per 32 consecutive vertices of the whole batch; the pairs
+// whose named edge is missing are counted in their graph's counters
+__global__ void multi_validate_exist_kernel(MultiParams M) {
+  const unsigned lane = threadIdx.x & 31u;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  const uint64_t G = M.num_graphs;
+  const uint64_t V = M.vbase[G];
+  for (uint64_t w0 = warp * 32; w0 < V; w0 += nwarps * 32) {
+    const uint64_t gv = w0 + lane;
+    uint64_t g = 0;
+    uint32_t v = 0, m = kNone;
+    bool valid = false, sym = false;
+    if (gv < V) {
+      g = find_graph(M.vbase, G, gv);
+      const mm_graph_desc d = M.desc[g];
+      v = (uint32_t)(gv - M.vbase[g]);
+      m = d.mate[v];
+      valid = m != kNone && m < d.n && m != v;
+      sym = valid && d.mate[m] == v;
+    }
+    unsigned todo = __ballot_sync(kFull, valid && !(sym && m < v));
+    while (todo) {
+      const int j = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const uint64_t gj = __shfl_sync(kFull, g, j);
+      const uint32_t vj = __shfl_sync(kFull, v, j), mj = __shfl_sync(kFull, m, j);
+      const bool sj = __shfl_sync(kFull, sym ? 1u : 0u, j) != 0u;
+      const mm_graph_desc d = M.desc[gj];
+      const int64_t dv = d.offsets[vj + 1] - d.offsets[vj];
+      const int64_t dm = d.offsets[mj + 1] - d.offsets[mj];
+      const bool v_first = dv <= dm;  // the shorter row first
+      bool hit = warp_row_has(d.offsets, d.nbrs, v_first ? vj : mj, v_first ? mj : vj, lane);
+      if (!hit) hit = warp_row_has(d.offsets, d.nbrs, v_first ? mj : vj, v_first ? vj : mj, lane);
+      if (!hit && lane == 0) {
+        unsigned long long* c = M.counters + gj * C_N;
+        atomicAdd(c + C_NONEDGE, sj ? 2ull : 1ull);
+        atomicMin(c + C_FIRST_BAD, (unsigned long long)vj);
+      }
+    }
+  }
+}
+
+// the checker's vertex pass on every vertex of every graph (range, symmetry,
+// pairs), counters kept per graph
 __global__ void multi_validate_kernel(MultiParams M) {
   const uint64_t G = M.num_graphs;
   const uint64_t V = M.vbase[G];
@@ -204,14 +240,13 @@ __global__ void multi_validate_kernel(MultiParams M) {
   for (uint64_t v0 = (uint64_t)blockIdx.x * blockDim.x; v0 < V; v0 += stride) {
     const uint64_t gv = v0 + threadIdx.x;
     uint64_t g = ~0ull;
-    uint32_t matched = 0, pair = 0, range = 0, asym = 0, nonedge = 0;
+    uint32_t matched = 0, pair = 0, range = 0, asym = 0;
     uint64_t first_bad = ~0ull;
     if (gv < V) {
       g = find_graph(M.vbase, G, gv);
       const mm_graph_desc d = M.desc[g];
       const uint64_t v = gv - M.vbase[g];
       const uint64_t n = d.n;
-      const unsigned char* found = M.found + M.vbase[g];
       const uint32_t m = d.mate[v];
       if (m != kNone) {
         if (m >= n || m == v) {
@@ -225,10 +260,6 @@ __global__ void multi_validate_kernel(MultiParams M) {
           } else if (v < m) {
             pair = 1;
           }
-          if (!found[v] && !found[m]) {
-            nonedge = 1;
-            first_bad = v;
-          }
         }
       }
     }
@@ -240,7 +271,6 @@ __global__ void multi_validate_kernel(MultiParams M) {
       group_add(c + C_PAIRS, peers, pair);
       group_add(c + C_RANGE, peers, range);
       group_add(c + C_ASYM, peers, asym);
-      group_add(c + C_NONEDGE, peers, nonedge);
       if (first_bad != ~0ull) atomicMin(c + C_FIRST_BAD, (unsigned long long)first_bad);
     }
   }
@@ -312,8 +342,6 @@ struct mm_multi {
   uint64_t pool_cap = 0;
   unsigned long long* counters = nullptr;
   uint64_t counters_cap = 0;
-  unsigned char* found = nullptr;
-  uint64_t found_cap = 0;
   unsigned long long* ctrl = nullptr;  // [0] work, [1] err
   uint32_t* h_err = nullptr;           // pinned
   unsigned long long* h_counters = nullptr;
@@ -387,7 +415,6 @@ MultiParams params(mm_multi* m, const TableSet& t, uint64_t G, const Layout& L, 
   M.err = reinterpret_cast<uint32_t*>(m->ctrl + 1);
   M.spin_limit = spin;
   M.counters = m->counters;
-  M.found = m->found;
   return M;
 }
 
@@ -505,7 +532,6 @@ mm_status mm_validate_multi_async(mm_multi* m, uint64_t num_graphs, const mm_gra
   Layout L;
   if ((st = stage_tables(&m->check, num_graphs, h_descs, kCheckGrain, 32, s, &L)) != MM_OK) return st;
   MTRY(grow(&m->counters, &m->counters_cap, num_graphs * C_N, s));
-  MTRY(grow(&m->found, &m->found_cap, L.total_vertices + 16, s));
   MTRY(grow(&m->check.part, &m->check.part_cap, 2 * (L.units + 1), s));
   MTRY(grow(&m->check.gid, &m->check.gid_cap, L.units + 1, s));
   if (m->h_counters_cap < num_graphs * C_N) {
@@ -523,11 +549,11 @@ mm_status mm_validate_multi_async(mm_multi* m, uint64_t num_graphs, const mm_gra
   const int grid = m->num_sms * 8;
   multi_counters_init_kernel<<<m->num_sms * 4, 256, 0, s>>>(m->counters, num_graphs);
   if (L.total_vertices) {
-    multi_clear_found_kernel<<<grid, 256, 0, s>>>(M);
     if (L.units) {
       multi_partition_kernel<<<grid, 256, 0, s>>>(M);
       multi_validate_edges_kernel<<<grid, 256, 0, s>>>(M);
     }
+    multi_validate_exist_kernel<<<grid, 256, 0, s>>>(M);
     multi_validate_kernel<<<grid, 256, 0, s>>>(M);
   }
   MTRY(cudaGetLastError());
@@ -584,7 +610,6 @@ mm_status mm_multi_destroy(mm_multi* m) {
   }
   if (m->pool) cudaFree(m->pool);
   if (m->counters) cudaFree(m->counters);
-  if (m->found) cudaFree(m->found);
   if (m->ctrl) cudaFree(m->ctrl);
   if (m->h_err) cudaFreeHost(m->h_err);
   if (m->h_counters) cudaFreeHost(m->h_counters);
