@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-edge-list", action="store_true")
+    ap.add_argument("--served-in-place-max-nnz", type=int, default=1 << 20)
     ap.add_argument("--symmetric-steps", type=int, default=50)
     ap.add_argument("--edge-list-steps", type=int, default=20)
     ap.add_argument("--edge-list-bits", type=int, default=2)
@@ -475,7 +476,7 @@ def run_served(args, skp, min_edges=None, max_edges=None, seconds=None, rate=Non
             submit(p, t0 + tt)
         return t0, finish()
 
-    srv = Server(status_bits=args.bits, grain=2048)
+    srv = Server(status_bits=args.bits, grain=2048, in_place_max_nnz=args.served_in_place_max_nnz)
     outs = [torch.empty(x[2], dtype=torch.int32, pin_memory=True) for x in pool]  # result buffers, reused
     reqs = []      # (request, scheduled arrival): latency counts from the schedule, as in the serial run
     t0, _ = run_trace(lambda p, at: reqs.append((srv.submit(pool[p][0], pool[p][1], outs[p]), at)),

@@ -278,6 +278,70 @@ mm_status map_host(const T** p, const char* what) {
   return MM_OK;
 }
 
+mm_status check_flags_and_device(uint32_t flags) {
+  if (flags & ~(MM_CHECK_CSR | MM_HOST_MAPPED)) return fail(MM_ERR_ARG, "unknown flags 0x%x", flags);
+  int ndev = 0;
+  CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (ndev <= 0) return fail(MM_ERR_CUDA, "no CUDA device");
+  return MM_OK;
+}
+
+// A handle with the scratch every input form needs: state words (one byte a
+// vertex, the widest packed layout), control words, compaction tiles, pinned
+// status words and events.  On failure nothing is left allocated.
+mm_status new_handle(uint64_t n, uint64_t items, cudaStream_t s, mm_graph** out) {
+  mm_graph* g = new (std::nothrow) mm_graph();
+  if (!g) return fail(MM_ERR_OOM, "host allocation failed");
+  auto step = [&](cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return MM_OK;
+    mm_destroy(g);
+    return fail(e == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+  };
+  mm_status st;
+  if ((st = step(cudaGetDevice(&g->device), "cudaGetDevice")) != MM_OK) return st;
+  if ((st = step(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device),
+                 "cudaDeviceGetAttribute")) != MM_OK)
+    return st;
+  g->n = n;
+  g->nnz = items;
+  const uint64_t words = (n + 3) / 4 + 4;
+  if ((st = step(cudaMalloc(&g->state, words * sizeof(uint32_t)), "state")) != MM_OK) return st;
+  if ((st = step(cudaMalloc(&g->ctrl, 32 * sizeof(unsigned long long)), "control words")) != MM_OK) return st;
+  if ((st = step(cudaMemsetAsync(g->ctrl, 0, 32 * sizeof(unsigned long long), s), "control words")) != MM_OK)
+    return st;
+  g->tile_cap = (n + kCompactTile - 1) / kCompactTile + 1;
+  if ((st = step(cudaMalloc(&g->tile_counts, g->tile_cap * sizeof(uint64_t)), "tiles")) != MM_OK) return st;
+  if ((st = step(cudaMallocHost(&g->h_err, 64), "pinned status")) != MM_OK) return st;
+  if ((st = step(cudaMallocHost(&g->h_counters, 16 * sizeof(unsigned long long)), "pinned counters")) != MM_OK)
+    return st;
+  *g->h_err = 0;
+  for (auto& e : g->ev)
+    if ((st = step(cudaEventCreate(&e), "events")) != MM_OK) return st;
+  *out = g;
+  return MM_OK;
+}
+
+// Run an input check launched on s (its count of violations in the control
+// words) and wait for it; on violations the handle is released and the call
+// fails with MM_ERR_BAD_GRAPH (msg takes the count).
+mm_status device_check(mm_graph* g, cudaStream_t s, cudaError_t launched, const char* msg) {
+  cudaError_t e = launched;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g->h_counters, csr_bad_ptr(g), sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    mm_destroy(g);
+    return fail(MM_ERR_CUDA, "input check: %s", cudaGetErrorString(e));
+  }
+  if (g->h_counters[0] != 0) {
+    const unsigned long long bad = g->h_counters[0];
+    mm_destroy(g);
+    return fail(MM_ERR_BAD_GRAPH, msg, bad);
+  }
+  return MM_OK;
+}
+
 mm_status check_handle(const mm_graph* g) {
   if (!g) return fail(MM_ERR_ARG, "null handle");
   int dev = -1;
@@ -380,10 +444,7 @@ mm_status mm_create_coo(uint64_t n, uint64_t m, const uint32_t* d_src, const uin
   };
   mm_status ms = (flags & MM_HOST_MAPPED) ? MM_OK : aligned();
   if (ms != MM_OK) return ms;
-  if (flags & ~(MM_CHECK_CSR | MM_HOST_MAPPED)) return fail(MM_ERR_ARG, "unknown flags 0x%x", flags);
-  int ndev = 0;
-  CUDA_TRY(cudaGetDeviceCount(&ndev));
-  if (ndev <= 0) return fail(MM_ERR_CUDA, "no CUDA device");
+  if ((ms = check_flags_and_device(flags)) != MM_OK) return ms;
   if ((flags & MM_HOST_MAPPED) && m) {  // the device addresses of the caller's page-locked arrays
     ms = map_host(&d_src, "src");
     if (ms == MM_OK) ms = map_host(&d_dst, "dst");
@@ -391,47 +452,16 @@ mm_status mm_create_coo(uint64_t n, uint64_t m, const uint32_t* d_src, const uin
     if (ms != MM_OK) return ms;
   }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-
-  mm_graph* g = new (std::nothrow) mm_graph();
-  if (!g) return fail(MM_ERR_OOM, "host allocation failed");
-  auto bail = [&](mm_status code) {
-    mm_destroy(g);
-    return code;
-  };
-#define CREATE_TRY(expr)                                                                   \
-  do {                                                                                     \
-    cudaError_t e_ = (expr);                                                               \
-    if (e_ != cudaSuccess)                                                                 \
-      return bail(fail(e_ == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA, "%s: %s", \
-                       #expr, cudaGetErrorString(e_)));                                    \
-  } while (0)
-  CREATE_TRY(cudaGetDevice(&g->device));
-  CREATE_TRY(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device));
+  mm_graph* g = nullptr;
+  if ((ms = new_handle(n, m, s, &g)) != MM_OK) return ms;
   g->coo = true;
-  g->n = n;
-  g->nnz = m;
   g->src = d_src;
   g->dst = d_dst;
-  const uint64_t words = (n + 3) / 4 + 4;
-  CREATE_TRY(cudaMalloc(&g->state, words * sizeof(uint32_t)));
-  CREATE_TRY(cudaMalloc(&g->ctrl, 32 * sizeof(unsigned long long)));
-  CREATE_TRY(cudaMemsetAsync(g->ctrl, 0, 32 * sizeof(unsigned long long), s));
-  g->tile_cap = (n + kCompactTile - 1) / kCompactTile + 1;
-  CREATE_TRY(cudaMalloc(&g->tile_counts, g->tile_cap * sizeof(uint64_t)));
-  CREATE_TRY(cudaMallocHost(&g->h_err, 64));
-  CREATE_TRY(cudaMallocHost(&g->h_counters, 16 * sizeof(unsigned long long)));
-  *g->h_err = 0;
-  for (auto& e : g->ev) CREATE_TRY(cudaEventCreate(&e));
   if (flags & MM_CHECK_CSR) {
-    CREATE_TRY(launch_coo_check(n, m, d_src, d_dst, csr_bad_ptr(g), prepare_grid(g), s));
-    CREATE_TRY(cudaMemcpyAsync(g->h_counters, csr_bad_ptr(g), sizeof(unsigned long long),
-                               cudaMemcpyDeviceToHost, s));
-    CREATE_TRY(cudaStreamSynchronize(s));
-    if (g->h_counters[0] != 0)
-      return bail(fail(MM_ERR_BAD_GRAPH, "edge-list check failed: %llu endpoint ids >= n",
-                       g->h_counters[0]));
+    ms = device_check(g, s, launch_coo_check(n, m, d_src, d_dst, csr_bad_ptr(g), prepare_grid(g), s),
+                      "edge-list check failed: %llu endpoint ids >= n");
+    if (ms != MM_OK) return ms;
   }
-#undef CREATE_TRY
   *out = g;
   return MM_OK;
 }
@@ -452,10 +482,7 @@ mm_status mm_create_csr(uint64_t n, uint64_t nnz, const int64_t* d_offsets, cons
   };
   mm_status ms = (flags & MM_HOST_MAPPED) ? MM_OK : aligned();
   if (ms != MM_OK) return ms;
-  if (flags & ~(MM_CHECK_CSR | MM_HOST_MAPPED)) return fail(MM_ERR_ARG, "unknown flags 0x%x", flags);
-  int ndev = 0;
-  CUDA_TRY(cudaGetDeviceCount(&ndev));
-  if (ndev <= 0) return fail(MM_ERR_CUDA, "no CUDA device");
+  if ((ms = check_flags_and_device(flags)) != MM_OK) return ms;
   if (flags & MM_HOST_MAPPED) {  // the device addresses of the caller's page-locked arrays
     ms = map_host(&d_offsets, "offsets");
     if (ms == MM_OK && nnz) ms = map_host(&d_nbrs, "nbrs");
@@ -463,50 +490,20 @@ mm_status mm_create_csr(uint64_t n, uint64_t nnz, const int64_t* d_offsets, cons
     if (ms != MM_OK) return ms;
   }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-
-  mm_graph* g = new (std::nothrow) mm_graph();
-  if (!g) return fail(MM_ERR_OOM, "host allocation failed");
-  mm_status st = MM_OK;
-  auto bail = [&](mm_status code) {
-    mm_destroy(g);
-    return code;
-  };
-#define CREATE_TRY(expr)                                                                   \
-  do {                                                                                     \
-    cudaError_t e_ = (expr);                                                               \
-    if (e_ != cudaSuccess)                                                                 \
-      return bail(fail(e_ == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA, "%s: %s", \
-                       #expr, cudaGetErrorString(e_)));                                    \
-  } while (0)
-  CREATE_TRY(cudaGetDevice(&g->device));
-  CREATE_TRY(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device));
-  g->n = n;
-  g->nnz = nnz;
+  mm_graph* g = nullptr;
+  if ((ms = new_handle(n, nnz, s, &g)) != MM_OK) return ms;
   g->offsets = d_offsets;
   g->nbrs = d_nbrs;
-  const uint64_t words = (n + 3) / 4 + 4;
-  CREATE_TRY(cudaMalloc(&g->state, words * sizeof(uint32_t)));
-  CREATE_TRY(cudaMalloc(&g->ctrl, 32 * sizeof(unsigned long long)));
-  CREATE_TRY(cudaMemsetAsync(g->ctrl, 0, 32 * sizeof(unsigned long long), s));
-  g->tile_cap = (n + kCompactTile - 1) / kCompactTile + 1;
-  CREATE_TRY(cudaMalloc(&g->tile_counts, g->tile_cap * sizeof(uint64_t)));
-  CREATE_TRY(cudaMallocHost(&g->h_err, 64));
-  CREATE_TRY(cudaMallocHost(&g->h_counters, 16 * sizeof(unsigned long long)));
-  *g->h_err = 0;
-  for (auto& e : g->ev) CREATE_TRY(cudaEventCreate(&e));
-  st = ensure_part(g, (n + nnz + kDefaultGrain - 1) / kDefaultGrain);
-  if (st != MM_OK) return bail(st);
-
-  if (flags & MM_CHECK_CSR) {
-    CREATE_TRY(launch_csr_check(n, nnz, d_offsets, d_nbrs, csr_bad_ptr(g), prepare_grid(g), s));
-    CREATE_TRY(cudaMemcpyAsync(g->h_counters, csr_bad_ptr(g), sizeof(unsigned long long),
-                               cudaMemcpyDeviceToHost, s));
-    CREATE_TRY(cudaStreamSynchronize(s));
-    if (g->h_counters[0] != 0)
-      return bail(fail(MM_ERR_BAD_GRAPH, "CSR check failed: %llu violations (offsets[0] = 0, "
-                       "non-decreasing, offsets[n] = nnz, ids < n)", g->h_counters[0]));
+  if ((ms = ensure_part(g, (n + nnz + kDefaultGrain - 1) / kDefaultGrain)) != MM_OK) {
+    mm_destroy(g);
+    return ms;
   }
-#undef CREATE_TRY
+  if (flags & MM_CHECK_CSR) {
+    ms = device_check(g, s, launch_csr_check(n, nnz, d_offsets, d_nbrs, csr_bad_ptr(g), prepare_grid(g), s),
+                      "CSR check failed: %llu violations (offsets[0] = 0, non-decreasing, "
+                      "offsets[n] = nnz, ids < n)");
+    if (ms != MM_OK) return ms;
+  }
   *out = g;
   return MM_OK;
 }
