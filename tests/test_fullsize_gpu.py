@@ -74,15 +74,35 @@ def _check_sampled_vertices(g, mate, k, seed):
     return int(matched.sum())
 
 
-def test_csr_rmat27_in_the_benchmark_launch(skp, rmat27):
+@pytest.mark.parametrize("symmetric", [0, 1])
+def test_csr_rmat27_in_the_benchmark_launch(skp, rmat27, symmetric):
     g = rmat27
     with skp.Graph(g.offsets, g.nbrs, check=False) as h:
-        mate = h.skipper(**BENCH_OPTS)
+        mate = h.skipper(symmetric=symmetric, **BENCH_OPTS)
         v = h.validate(mate)
     assert v.flags == 0, v.as_dict()
     m = mate.cpu().numpy().view(np.uint32)
     assert 2 * v.n_pairs == int((m != NONE).sum())
-    assert _check_sampled_vertices(g, m, 200_000, seed=3) > 0
+    assert _check_sampled_vertices(g, m, 200_000, seed=3 + symmetric) > 0
+
+
+def test_csr_rmat27_read_in_place_from_host_memory(skp, rmat27):
+    """The end-to-end path of the benchmark: the CSR in pinned host memory, read
+    in place by the kernels (MM_HOST_MAPPED) through the host session."""
+    g = rmat27
+    h_off = g.offsets.cpu().pin_memory()
+    h_nb = g.nbrs.cpu().pin_memory()
+    sess = skp.HostSession(g.n, g.nnz)
+    try:
+        m_host = sess.run(h_off, h_nb, **BENCH_OPTS)
+        assert sess.last_mode == "host_mapped"
+        with skp.Graph(g.offsets, g.nbrs, check=False) as h:
+            v = h.validate(m_host.cuda())
+        assert v.flags == 0, v.as_dict()
+        assert _check_sampled_vertices(g, m_host.numpy().view(np.uint32), 100_000, seed=7) > 0
+    finally:
+        sess.close()
+        del h_off, h_nb
 
 
 def test_edge_list_rmat27_raw_draws_in_the_benchmark_launch(skp, rmat27):
