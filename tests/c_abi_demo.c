@@ -1,0 +1,115 @@
+/*
+ * c_abi_demo.c -- the C ABI used from plain C, with no Python and no torch:
+ * device buffers from the CUDA runtime, the library's calls on them.
+ *
+ * The graph is the one Section II-B walks through (Fig. 1): vertices 0..3,
+ * edges 01 02 03 12 23, stored as a symmetric CSR with ascending rows.
+ * Serial mode must give sequential greedy matching's result, mate = 1 0 3 2;
+ * the parallel pass must give a maximal matching the checker accepts; the
+ * same edges as a list must do the same; and the native server must return
+ * the serial result for a host-memory request.
+ *
+ * Prints "ok" and exits 0, or prints what failed and exits 1.
+ */
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <cuda_runtime.h>
+
+#include "skipper.h"
+
+static int failed(const char *what, mm_status st)
+{
+    printf("%s: status %d: %s\n", what, (int)st, mm_last_error());
+    return 1;
+}
+
+int main(void)
+{
+    const int64_t h_off[5] = {0, 3, 5, 8, 10};
+    const uint32_t h_nb[10] = {1, 2, 3, 0, 2, 0, 1, 3, 0, 2};
+    const uint32_t expect[4] = {1, 0, 3, 2};
+    int64_t *d_off = NULL;
+    uint32_t *d_nb = NULL, *d_mate = NULL, *d_src = NULL, *d_dst = NULL;
+    uint32_t mate[4];
+    if (cudaMalloc((void **)&d_off, sizeof h_off) != cudaSuccess ||
+        cudaMalloc((void **)&d_nb, sizeof h_nb) != cudaSuccess ||
+        cudaMalloc((void **)&d_mate, sizeof mate) != cudaSuccess) {
+        printf("cudaMalloc failed\n");
+        return 1;
+    }
+    cudaMemcpy(d_off, h_off, sizeof h_off, cudaMemcpyHostToDevice);
+    cudaMemcpy(d_nb, h_nb, sizeof h_nb, cudaMemcpyHostToDevice);
+
+    mm_graph *g = NULL;
+    mm_status st = mm_create_csr(4, 10, d_off, d_nb, MM_CHECK_CSR, NULL, &g);
+    if (st != MM_OK) return failed("mm_create_csr", st);
+    mm_options o;
+    mm_default_options(&o);
+    o.serial = 1;
+    if ((st = mm_skipper(g, &o, d_mate, NULL, 0, NULL, NULL)) != MM_OK) return failed("mm_skipper serial", st);
+    cudaMemcpy(mate, d_mate, sizeof mate, cudaMemcpyDeviceToHost);
+    if (memcmp(mate, expect, sizeof mate) != 0) {
+        printf("serial mate %u %u %u %u, expected 1 0 3 2\n", mate[0], mate[1], mate[2], mate[3]);
+        return 1;
+    }
+    o.serial = 0;
+    if ((st = mm_skipper(g, &o, d_mate, NULL, 0, NULL, NULL)) != MM_OK) return failed("mm_skipper", st);
+    mm_verdict v;
+    if ((st = mm_validate(g, d_mate, NULL, 0, &v, NULL)) != MM_OK) return failed("mm_validate", st);
+    if (v.flags != 0 || v.n_pairs != 2) {
+        printf("parallel verdict flags %u pairs %llu\n", v.flags, (unsigned long long)v.n_pairs);
+        return 1;
+    }
+    mm_destroy(g);
+
+    /* the same edges as a list (each once, one reversed) */
+    const uint32_t h_src[5] = {0, 2, 0, 2, 2};
+    const uint32_t h_dst[5] = {1, 0, 3, 1, 3};
+    cudaMalloc((void **)&d_src, sizeof h_src);
+    cudaMalloc((void **)&d_dst, sizeof h_dst);
+    cudaMemcpy(d_src, h_src, sizeof h_src, cudaMemcpyHostToDevice);
+    cudaMemcpy(d_dst, h_dst, sizeof h_dst, cudaMemcpyHostToDevice);
+    if ((st = mm_create_coo(4, 5, d_src, d_dst, MM_CHECK_CSR, NULL, &g)) != MM_OK)
+        return failed("mm_create_coo", st);
+    o.serial = 1;
+    if ((st = mm_skipper(g, &o, d_mate, NULL, 0, NULL, NULL)) != MM_OK) return failed("edge list serial", st);
+    cudaMemcpy(mate, d_mate, sizeof mate, cudaMemcpyDeviceToHost);
+    if (memcmp(mate, expect, sizeof mate) != 0) {   /* (0,1) first, then (2,3) */
+        printf("edge-list serial mate %u %u %u %u\n", mate[0], mate[1], mate[2], mate[3]);
+        return 1;
+    }
+    if ((st = mm_validate(g, d_mate, NULL, 0, &v, NULL)) != MM_OK || v.flags != 0)
+        return failed("edge-list mm_validate", st);
+    mm_destroy(g);
+
+    /* one request through the native server, from host memory */
+    mm_server_config c;
+    mm_server_default_config(&c);
+    c.opts.serial = 1;
+    c.memory_bytes = 64u << 20;
+    mm_server *s = NULL;
+    if ((st = mm_server_create(&c, &s)) != MM_OK) return failed("mm_server_create", st);
+    uint32_t out[4] = {7, 7, 7, 7};
+    uint64_t ticket = 0;
+    if ((st = mm_server_submit(s, 4, 10, h_off, h_nb, out, &ticket)) != MM_OK)
+        return failed("mm_server_submit", st);
+    mm_server_result r;
+    if ((st = mm_server_wait(s, ticket, 60.0, &r)) != MM_OK) return failed("mm_server_wait", st);
+    if (r.status != MM_OK || r.verdict.flags != 0 || memcmp(out, expect, sizeof out) != 0 ||
+        r.done_ns < r.submit_ns) {
+        printf("server: status %d flags %u mate %u %u %u %u\n", (int)r.status, r.verdict.flags,
+               out[0], out[1], out[2], out[3]);
+        return 1;
+    }
+    if ((st = mm_server_destroy(s)) != MM_OK) return failed("mm_server_destroy", st);
+
+    cudaFree(d_off);
+    cudaFree(d_nb);
+    cudaFree(d_mate);
+    cudaFree(d_src);
+    cudaFree(d_dst);
+    printf("ok\n");
+    return 0;
+}
