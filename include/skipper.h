@@ -141,6 +141,11 @@ typedef struct mm_stats {
     uint64_t conflicted_entries;
     uint64_t max_conflicts;     /* on one entry */
     uint64_t hist[10];
+    uint64_t transitions[4];    /* state transitions made (Fig. 4): ACC->RSVD (line 11),
+                                   ACC->MCHD (line 14), RSVD->MCHD (line 15),
+                                   RSVD->ACC (line 18); the holder's two are checked
+                                   on the word their atomic returns */
+    uint64_t illegal_transitions;  /* commits / releases that did not find RSVD (0) */
 } mm_stats;
 
 /*
@@ -301,6 +306,14 @@ mm_status mm_sync(mm_graph *g, void *cuda_stream);
 /* Statistics of the last mm_skipper call made with o->stats = 1 (waits for it).
  * MM_ERR_ARG when no such call was made. */
 mm_status mm_get_stats(mm_graph *g, mm_stats *out, void *cuda_stream);
+
+/* Debugging aid: counts of the states the last mm_skipper call on g left in
+ * its state array (the handle's packed states, or the mate array itself in
+ * the 32-bit layout): out[0] ACC, out[1] RSVD, out[2] MCHD, out[3] any other
+ * field value (never produced).  After a completed call RSVD is 0 and MCHD is
+ * twice the matched pairs (Fig. 4: every reservation ends in MCHD or ACC).
+ * Synchronous.  MM_ERR_ARG when no mm_skipper call was made on g. */
+mm_status mm_state_census(mm_graph *g, uint64_t out[4], void *cuda_stream);
 
 /* Per-kernel times of the last call made with o->timing = 1 (waits for its
  * events).  MM_ERR_ARG when no timed call was made since the last

@@ -187,6 +187,13 @@ class Graph:
         _check(lib.mm_get_stats(self._h, ctypes.byref(st), _stream_ptr(stream)), "mm_get_stats")
         return st.as_dict()
 
+    def state_census(self, stream=None) -> dict:
+        """Counts of the states the last skipper() call left (mm_state_census):
+        after a completed call no vertex is RSVD and MCHD is twice the pairs."""
+        out = (ctypes.c_uint64 * 4)()
+        _check(lib.mm_state_census(self._h, out, _stream_ptr(stream)), "mm_state_census")
+        return {"acc": int(out[0]), "rsvd": int(out[1]), "mchd": int(out[2]), "other": int(out[3])}
+
     @staticmethod
     def _tdict(t) -> dict:
         return {"init_ms": t.init_ms, "sweep_ms": t.sweep_ms, "compact_ms": t.compact_ms,

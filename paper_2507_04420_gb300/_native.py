@@ -169,11 +169,14 @@ class Stats(ctypes.Structure):
         ("conflicted_entries", ctypes.c_uint64),
         ("max_conflicts", ctypes.c_uint64),
         ("hist", ctypes.c_uint64 * 10),
+        ("transitions", ctypes.c_uint64 * 4),
+        ("illegal_transitions", ctypes.c_uint64),
     ]
 
     def as_dict(self):
-        d = {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "hist"}
+        d = {k: int(getattr(self, k)) for k, _ in self._fields_ if k not in ("hist", "transitions")}
         d["hist"] = [int(x) for x in self.hist]
+        d["transitions"] = [int(x) for x in self.transitions]
         return d
 
 
@@ -186,6 +189,7 @@ SYMBOLS = [
     ("mm_create_csr", _I, [_U64, _U64, _P, _P, _U32, _P, ctypes.POINTER(_P)]),
     ("mm_create_coo", _I, [_U64, _U64, _P, _P, _U32, _P, ctypes.POINTER(_P)]),
     ("mm_host_device_address", _I, [_P, ctypes.POINTER(_P)]),
+    ("mm_state_census", _I, [_P, ctypes.POINTER(_U64), _P]),
     ("mm_skipper", _I, [_P, ctypes.POINTER(Options), _P, _P, _U64, _P, _P]),
     ("mm_skipper_batched", _I, [_P, _U64, _P, _P, ctypes.POINTER(Options), _P, _P, _P]),
     ("mm_validate", _I, [_P, _P, _P, _U64, ctypes.POINTER(Verdict), _P]),

@@ -78,6 +78,8 @@ struct mm_graph {
   uint32_t* seen_bits = nullptr;
   unsigned long long* stats = nullptr;  // sweep statistics, allocated on first stats call
   bool stats_valid = false;
+  int last_bits = 0;                   // layout and state array of the last mm_skipper call
+  const uint32_t* last_state = nullptr;
   unsigned char* found = nullptr;      // checker scratch, allocated on first mm_validate
   int64_t* check_part = nullptr;
   uint64_t* tile_counts = nullptr;
@@ -377,6 +379,8 @@ mm_status skipper_coo(mm_graph* g, const Resolved& r, uint32_t* d_mate, uint32_t
     g->stats_valid = true;
   }
   CheckScratch cs{counters_ptr(g), g->seen_bits, g->tile_counts, g->tile_cap, nullptr, nullptr};
+  g->last_bits = r.bits;
+  g->last_state = C.P.state;
   cudaEvent_t* ev = nullptr;
   if (r.timing) {
     if ((st = ensure_hist(g)) != MM_OK) return st;
@@ -530,6 +534,8 @@ mm_status mm_skipper(mm_graph* g, const mm_options* o, uint32_t* d_mate, uint32_
   }
 
   CheckScratch cs{counters_ptr(g), g->seen_bits, g->tile_counts, g->tile_cap, nullptr, nullptr};
+  g->last_bits = r.bits;
+  g->last_state = P.state;
   cudaEvent_t* ev = nullptr;
   if (r.timing) {
     if ((st = ensure_hist(g)) != MM_OK) return st;
@@ -571,6 +577,21 @@ mm_status mm_get_stats(mm_graph* g, mm_stats* out, void* cuda_stream) {
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   CUDA_TRY(cudaMemcpyAsync(out, g->stats, sizeof(mm_stats), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
+  return MM_OK;
+}
+
+mm_status mm_state_census(mm_graph* g, uint64_t out[4], void* cuda_stream) {
+  g_err[0] = 0;
+  mm_status st = check_handle(g);
+  if (st != MM_OK) return st;
+  if (!out) return fail(MM_ERR_ARG, "null out");
+  if (!g->last_state && g->n) return fail(MM_ERR_ARG, "no mm_skipper call on this handle");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  unsigned long long* d = counters_ptr(g);  // the checker's counters, free between calls
+  CUDA_TRY(launch_census(g->last_state, g->n, g->last_bits ? g->last_bits : 8, d, prepare_grid(g), s));
+  CUDA_TRY(cudaMemcpyAsync(g->h_counters, d, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  for (int k = 0; k < 4; ++k) out[k] = g->h_counters[k];
   return MM_OK;
 }
 

@@ -362,6 +362,42 @@ cudaError_t launch_validate_coo(uint64_t n, uint64_t m, const uint32_t* src, con
   return cudaGetLastError();
 }
 
+namespace {
+
+// Census of a state array: out[0..3] = ACC, RSVD, MCHD, other field values.
+__global__ void census_kernel(const uint32_t* __restrict__ state, uint64_t n, int bits,
+                              unsigned long long* __restrict__ out) {
+  unsigned long long c[4] = {0, 0, 0, 0};
+  const uint64_t per = bits == 32 ? 1 : 32u / (uint32_t)bits;
+  const uint32_t mask = bits == 32 ? 0u : (1u << bits) - 1u;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t w = state[v / per];
+    int k;
+    if (bits == 32) {
+      k = w == kWAcc ? 0 : (w == kWRsvd ? 1 : 2);
+    } else {
+      const uint32_t f = (w >> ((v % per) * (uint32_t)bits)) & mask;
+      k = f == kAcc ? 0 : f == kRsvd ? 1 : f == kMchd ? 2 : 3;
+    }
+    ++c[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const unsigned long long t = warp_sum64(c[k]);
+    if ((threadIdx.x & 31) == 0 && t) atomicAdd(out + k, t);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_census(const uint32_t* state, uint64_t n, int bits, unsigned long long* out,
+                          int grid, cudaStream_t s) {
+  zero_u64_kernel<<<1, 32, 0, s>>>(out, 4, 0ull);
+  if (n) census_kernel<<<grid, 256, 0, s>>>(state, n, bits, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_compact(uint64_t n, const uint32_t* mate, uint32_t* pairs, uint64_t cap,
                            uint64_t* count, const CheckScratch& cs, cudaStream_t s) {
   const uint64_t tiles = (n + kCompactTile - 1) / kCompactTile;

@@ -58,6 +58,8 @@ cudaError_t launch_coo_check(uint64_t n, uint64_t m, const uint32_t* src, const 
 cudaError_t launch_validate_coo(uint64_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
                                 const uint32_t* mate, const uint32_t* pairs, uint64_t count,
                                 const CheckScratch& cs, int grid, cudaStream_t s);
+cudaError_t launch_census(const uint32_t* state, uint64_t n, int bits, unsigned long long* out,
+                          int grid, cudaStream_t s);
 constexpr uint64_t kCompactTile = 4096;  // vertices per compaction tile
 cudaError_t launch_compact(uint64_t n, const uint32_t* mate, uint32_t* pairs, uint64_t cap,
                            uint64_t* count, const CheckScratch& cs, cudaStream_t s);

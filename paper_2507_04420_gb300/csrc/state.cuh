@@ -69,7 +69,9 @@ enum StatSlot : int {
   kStConflicted,    // entries with at least one conflict
   kStMaxConflicts,  // most conflicts on one entry
   kStHist,          // 10 bins: 1, 2, 3-4, 5-8, 9-16, 17-32, 33-64, 65-128, 129-256, >256
-  kStCount = kStHist + 10
+  kStTrans = kStHist + 10,  // state transitions (Fig. 4): ACC->RSVD, ACC->MCHD, RSVD->MCHD, RSVD->ACC
+  kStIllegal = kStTrans + 4,  // commits / releases that found the field not RSVD
+  kStCount
 };
 
 __device__ __forceinline__ void stat_conflicts(unsigned long long* st, uint32_t c) {
@@ -203,6 +205,18 @@ struct PackedState {
   __device__ __forceinline__ void release(uint32_t u) const {
     atomicXor(words + word(u), (kRsvd ^ kAcc) << shift(u));
   }
+  // statistics instances: the same two transitions, each checked on the word
+  // its atomic returns (the field must have been RSVD)
+  __device__ __forceinline__ void commit_checked(uint32_t u, uint32_t v, unsigned long long* st) const {
+    mate[u] = v;
+    mate[v] = u;
+    const uint32_t old = atomicXor(words + word(u), (kRsvd ^ kMchd) << shift(u));
+    atomicAdd(st + (((old >> shift(u)) & kMask) == kRsvd ? kStTrans + 2 : kStIllegal), 1ull);
+  }
+  __device__ __forceinline__ void release_checked(uint32_t u, unsigned long long* st) const {
+    const uint32_t old = atomicXor(words + word(u), (kRsvd ^ kAcc) << shift(u));
+    atomicAdd(st + (((old >> shift(u)) & kMask) == kRsvd ? kStTrans + 3 : kStIllegal), 1ull);
+  }
 };
 
 // one state byte per vertex (the paper's layout) and a 2-bit field per vertex
@@ -232,6 +246,15 @@ struct WordState {
   }
   __device__ __forceinline__ void commit(uint32_t u, uint32_t v) const { st_relaxed(words + u, v); }
   __device__ __forceinline__ void release(uint32_t u) const { st_relaxed(words + u, kWAcc); }
+  // statistics instances: exchanges, so the word they replace can be checked
+  __device__ __forceinline__ void commit_checked(uint32_t u, uint32_t v, unsigned long long* st) const {
+    const uint32_t old = atomicExch(words + u, v);
+    atomicAdd(st + (old == kWRsvd ? kStTrans + 2 : kStIllegal), 1ull);
+  }
+  __device__ __forceinline__ void release_checked(uint32_t u, unsigned long long* st) const {
+    const uint32_t old = atomicExch(words + u, kWAcc);
+    atomicAdd(st + (old == kWRsvd ? kStTrans + 3 : kStIllegal), 1ull);
+  }
 };
 
 // Algorithm 1, lines 6-18, for one stored entry (x, y), given words rx, ry
@@ -266,10 +289,16 @@ __device__ __forceinline__ bool resolve_edge(const S& s, uint32_t x, uint32_t y,
       rv = s.raw(v);
       continue;
     }
+    if (kStats) atomicAdd(P.stats + kStTrans + 0, 1ull);  // ACC -> RSVD
     bool won = false, gave_up = false;
     for (;;) {                               // lines 13-16, holding u
       if (s.try_claim(v, u, rv, P)) {
-        s.commit(u, v);                      // lines 15-16
+        if (kStats) {
+          atomicAdd(P.stats + kStTrans + 1, 1ull);  // ACC -> MCHD (v)
+          s.commit_checked(u, v, P.stats);          // lines 15-16, RSVD -> MCHD (u)
+        } else {
+          s.commit(u, v);                      // lines 15-16
+        }
         won = true;
         break;
       }
@@ -286,7 +315,10 @@ __device__ __forceinline__ bool resolve_edge(const S& s, uint32_t x, uint32_t y,
       result = true;
       break;
     }
-    s.release(u);                            // lines 17-18
+    if (kStats)
+      s.release_checked(u, P.stats);         // lines 17-18, RSVD -> ACC
+    else
+      s.release(u);                          // lines 17-18
     result = gave_up ? false : !x_low;
     break;
   }

@@ -55,6 +55,8 @@ int main(void) {
          offsetof(mm_server_config, opts), offsetof(mm_server_config, reserved),
          sizeof(mm_server_result), offsetof(mm_server_result, verdict),
          offsetof(mm_server_result, done_ns), sizeof(mm_graph_desc));
+  printf("%zu %zu %zu\n", sizeof(mm_stats), offsetof(mm_stats, transitions),
+         offsetof(mm_stats, illegal_transitions));
   return 0;
 }
 """
@@ -69,7 +71,9 @@ int main(void) {
     assert vals == [ctypes.sizeof(O), O.spin_limit.offset, O.poison_vertex.offset,
                     ctypes.sizeof(V), V.first_uncovered.offset, ctypes.sizeof(T), T.units.offset,
                     O.symmetric.offset, ctypes.sizeof(C), C.opts.offset, C.reserved.offset,
-                    ctypes.sizeof(R), R.verdict.offset, R.done_ns.offset, ctypes.sizeof(G)]
+                    ctypes.sizeof(R), R.verdict.offset, R.done_ns.offset, ctypes.sizeof(G),
+                    ctypes.sizeof(native.Stats), native.Stats.transitions.offset,
+                    native.Stats.illegal_transitions.offset]
 
 
 def test_default_options_and_argument_errors(native):
