@@ -196,7 +196,8 @@ class Clocks:
 def make_graph(args, device):
     import graphgen as gg
     import torch
-    chunks = 16 if args.scale >= 26 else 1
+    # source-range chunks bound the CSR build's temporaries (same output for any count)
+    chunks = (16 << max(0, args.scale - 27)) if args.scale >= 26 else 1
     t = time.time()
     g = gg.rmat(args.scale, args.edge_factor, 0.57, 0.19, 0.19, seed=args.seed, device=device,
                 chunks=chunks)
