@@ -13,6 +13,7 @@ an unmatched vertex reads as -1 (0xFFFFFFFF).
 from __future__ import annotations
 
 import collections
+import contextlib
 import ctypes
 from typing import Optional
 
@@ -397,6 +398,11 @@ class HostSession:
         if n > self.n_max or nnz > self.nnz_max:
             raise ValueError("graph larger than the session's buffers")
         mate_d = self.d_mate[:n]
+        # the copies are enqueued on the stream the calls run on
+        with torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext():
+            return self._run(offsets, nbrs, mate_out, stream, check, n, nnz, mate_d, **kw)
+
+    def _run(self, offsets, nbrs, mate_out, stream, check, n, nnz, mate_d, **kw):
         if self.zero_copy and not check and offsets.is_pinned() and (nnz == 0 or nbrs.is_pinned()):
             self.last_mode = "host_mapped"
             key = (offsets.data_ptr(), nbrs.data_ptr(), n, nnz)

@@ -193,9 +193,20 @@ mm_status read_err(mm_graph* g, cudaStream_t s) {
 // L2 persisting window over the state array for the sweep (opt-in); the
 // stream attribute and the context's set-aside are put back afterwards.
 struct L2Window {
-  bool on = false;
+  bool on = false, limit_set = false;
   cudaStream_t s{};
   size_t old_limit = 0;
+  // a call that fails between open and close still puts the stream attribute
+  // and the set-aside back (quietly: the call's own error message stands)
+  ~L2Window() {
+    if (on) {
+      cudaStreamAttrValue a{};
+      a.accessPolicyWindow.num_bytes = 0;
+      cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &a);
+      cudaCtxResetPersistingL2Cache();
+    }
+    if (limit_set) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, old_limit);
+  }
   mm_status open(mm_graph* g, const Resolved& r, cudaStream_t st, const uint32_t* base, size_t bytes) {
     if (!r.l2_persist) return MM_OK;
     int max_win = 0, max_persist = 0;
@@ -205,6 +216,8 @@ struct L2Window {
     CUDA_TRY(cudaDeviceGetLimit(&old_limit, cudaLimitPersistingL2CacheSize));
     const size_t want = bytes < (size_t)max_persist ? bytes : (size_t)max_persist;
     CUDA_TRY(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want));
+    limit_set = true;
+    s = st;
     cudaStreamAttrValue a{};
     a.accessPolicyWindow.base_ptr = const_cast<uint32_t*>(base);
     a.accessPolicyWindow.num_bytes = bytes < (size_t)max_win ? bytes : (size_t)max_win;
@@ -215,17 +228,20 @@ struct L2Window {
     a.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
     CUDA_TRY(cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &a));
     on = true;
-    s = st;
     return MM_OK;
   }
   mm_status close() {
-    if (!on) return MM_OK;
-    on = false;
-    cudaStreamAttrValue a{};
-    a.accessPolicyWindow.num_bytes = 0;
-    CUDA_TRY(cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &a));
-    CUDA_TRY(cudaCtxResetPersistingL2Cache());
-    CUDA_TRY(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, old_limit));
+    if (on) {
+      on = false;
+      cudaStreamAttrValue a{};
+      a.accessPolicyWindow.num_bytes = 0;
+      CUDA_TRY(cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &a));
+      CUDA_TRY(cudaCtxResetPersistingL2Cache());
+    }
+    if (limit_set) {
+      limit_set = false;
+      CUDA_TRY(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, old_limit));
+    }
     return MM_OK;
   }
 };

@@ -370,11 +370,11 @@ mm_status stage_tables(TableSet* m, uint64_t G, const mm_graph_desc* h, uint64_t
     m->staging_pending = false;
   }
   if (m->staging_cap < L->bytes) {
+    uint64_t cap = m->staging_cap ? m->staging_cap : 4096;   // doubling from the old size
+    while (cap < L->bytes) cap *= 2;
     if (m->staging) cudaFreeHost(m->staging);
     m->staging = nullptr;
     m->staging_cap = 0;
-    uint64_t cap = m->staging_cap ? m->staging_cap : 4096;
-    while (cap < L->bytes) cap *= 2;
     MTRY(cudaMallocHost(&m->staging, cap));
     m->staging_cap = cap;
   }

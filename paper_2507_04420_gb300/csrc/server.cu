@@ -84,6 +84,7 @@ struct mm_server {
   char failure_msg[256] = "";
   std::thread worker;
 
+  std::vector<void*> orphans;      // device buffers of a failed launch (worker only)
   std::atomic<uint64_t> used{0};   // device bytes held by admitted requests (worker writes)
   std::atomic<uint64_t> ticks{0}, graphs{0};  // launches and graphs launched
 };
@@ -123,9 +124,31 @@ void finish(mm_server* s, Req& r, mm_status st, const mm_verdict* v) {
   s->done[r.ticket] = res;
 }
 
+// Device buffers of work that never reached a completed launch: the copy
+// buffers of staged requests and the arena of a launch that failed part way.
+// A failed launch may have enqueued work on them, so every server stream is
+// waited for first.  Errors are ignored: the server is already failing.
+void release_orphans(mm_server* s, std::vector<Req>& staged) {
+  for (Req& r : staged)
+    if (r.own) {
+      s->orphans.push_back(const_cast<int64_t*>(r.off));
+      s->orphans.push_back(const_cast<uint32_t*>(r.nb));
+      s->orphans.push_back(r.mate);
+      r.own = false;
+    }
+  if (s->orphans.empty()) return;
+  for (cudaStream_t st : {s->h2d, s->d2h, s->slot_stream[0], s->slot_stream[1]})
+    if (st) cudaStreamSynchronize(st);
+  for (void* p : s->orphans)
+    if (p) cudaFree(p);
+  s->orphans.clear();
+  cudaGetLastError();
+}
+
 // Everything the worker holds fails with `st` (a worker failure).
 void fail_all(mm_server* s, std::deque<Req>& pending, std::vector<Req>& staged,
               std::deque<Tick>& inflight, mm_status st) {
+  release_orphans(s, staged);
   for (Req& r : pending) finish(s, r, st, nullptr);
   for (Req& r : staged) finish(s, r, st, nullptr);
   for (Tick& t : inflight)
@@ -147,23 +170,24 @@ void fail_all(mm_server* s, std::deque<Req>& pending, std::vector<Req>& staged,
     cudaError_t e_ = (expr);                                                              \
     if (e_ != cudaSuccess) {                                                              \
       snprintf(s->failure_msg, sizeof s->failure_msg, "%s: %s", #expr, cudaGetErrorString(e_)); \
-      return MM_ERR_CUDA;                                                                 \
+      return e_ == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA;                  \
     }                                                                                     \
   } while (0)
 
 // copy path: the request's own device buffers, filled on the copy stream
 mm_status admit_copy(mm_server* s, Req& r) {
+  r.own = true;   // whatever of the three is allocated belongs to the request
   W_TRY(cudaMallocAsync((void**)&r.off, 8 * (r.n + 1), s->h2d));
   W_TRY(cudaMallocAsync((void**)&r.nb, 4 * (r.nnz ? r.nnz : 1), s->h2d));
   W_TRY(cudaMallocAsync((void**)&r.mate, 4 * (r.n ? r.n : 1), s->h2d));
-  r.own = true;
   W_TRY(cudaMemcpyAsync(const_cast<int64_t*>(r.off), r.h_off, 8 * (r.n + 1), cudaMemcpyHostToDevice, s->h2d));
   if (r.nnz)
     W_TRY(cudaMemcpyAsync(const_cast<uint32_t*>(r.nb), r.h_nb, 4 * r.nnz, cudaMemcpyHostToDevice, s->h2d));
   return MM_OK;
 }
 
-mm_status launch(mm_server* s, std::vector<Req>& staged, std::deque<Tick>& inflight) {
+mm_status launch_tick(mm_server* s, std::vector<Req>& staged, std::deque<Tick>& inflight,
+                      uint32_t** arena_out) {
   Tick t;
   t.slot = s->next_slot;
   s->next_slot = (s->next_slot + 1) % s->slots;
@@ -185,6 +209,7 @@ mm_status launch(mm_server* s, std::vector<Req>& staged, std::deque<Tick>& infli
   uint32_t* arena = nullptr;
   if (arena_n) {
     W_TRY(cudaMallocAsync((void**)&arena, 4 * arena_n, st));
+    *arena_out = arena;
     uint64_t at = 0;
     for (Req& r : staged)
       if (r.in_place) {
@@ -222,12 +247,17 @@ mm_status launch(mm_server* s, std::vector<Req>& staged, std::deque<Tick>& infli
   W_TRY(cudaEventRecord(t.back, s->d2h));
   W_TRY(cudaStreamWaitEvent(s->d2h, t.checked, 0));
   for (Req& r : staged)
-    if (r.own) {
+    if (r.own) {   // each pointer is dropped once its release is enqueued
       W_TRY(cudaFreeAsync(const_cast<int64_t*>(r.off), s->d2h));
+      r.off = nullptr;
       W_TRY(cudaFreeAsync(const_cast<uint32_t*>(r.nb), s->d2h));
+      r.nb = nullptr;
       W_TRY(cudaFreeAsync(r.mate, s->d2h));
+      r.mate = nullptr;
+      r.own = false;
     }
   if (arena) W_TRY(cudaFreeAsync(arena, s->d2h));
+  *arena_out = nullptr;
   s->event_pool.push_back(copied);   // recorded work keeps the event; reuse is stream-ordered
   s->event_pool.push_back(swept);
   s->ticks += 1;
@@ -235,6 +265,13 @@ mm_status launch(mm_server* s, std::vector<Req>& staged, std::deque<Tick>& infli
   t.reqs.swap(staged);
   inflight.push_back(std::move(t));
   return MM_OK;
+}
+
+mm_status launch(mm_server* s, std::vector<Req>& staged, std::deque<Tick>& inflight) {
+  uint32_t* arena = nullptr;
+  const mm_status st = launch_tick(s, staged, inflight, &arena);
+  if (st != MM_OK && arena) s->orphans.push_back(arena);
+  return st;
 }
 
 // the oldest tick, once its checker and its copies back are done

@@ -88,6 +88,25 @@ def test_host_session_zero_copy_and_copy_agree(skp):
         cp.close()
 
 
+def test_host_session_on_a_side_stream(skp):
+    """With stream= given, the session's copies run on that stream too: a busy
+    current stream (a sleep kernel enqueued on it) must not let the pass read
+    the previous graph's bytes out of the reused device buffers."""
+    a, b = gg.rmat(11, 8, seed=1), gg.erdos_renyi(2048, 7000, seed=2)
+    cp = skp.HostSession(max(a.n, b.n), max(a.nnz, b.nnz), zero_copy=False)
+    side = torch.cuda.Stream()
+    try:
+        for g in (a, b, a):
+            ref, _ = oracle.sgmm(g.offsets.numpy(), g.nbrs.numpy())
+            torch.cuda._sleep(50_000_000)            # about 25 ms on the current stream
+            m = cp.run(_pinned(g.offsets), _pinned(g.nbrs), stream=side, serial=1)
+            assert cp.last_mode == "copy"
+            assert np.array_equal(m.numpy().view(np.uint32), ref)
+        torch.cuda.synchronize()
+    finally:
+        cp.close()
+
+
 def _pageable_access():
     """cudaDevAttrPageableMemoryAccess: the device reads pageable host memory."""
     cudart = ctypes.CDLL("libcudart.so")

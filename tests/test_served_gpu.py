@@ -174,3 +174,44 @@ def test_server_many_client_threads(skp, graphs):
             assert r.verdict.flags == 0 and r.latency >= 0
     srv.close()
     assert srv.ticks >= 1 and srv.graphs_launched == sum(len(x) for x in out)
+
+
+def test_server_worker_failure_fails_requests_and_frees_device_memory(skp):
+    """A device allocation that fails inside the worker ends the serving loop
+    cleanly: the request fails with MM_ERR_OOM, later submits are refused,
+    destroy reports the failure, and the buffer already allocated for the
+    request is released.  The request is a copy-path graph of 2^31 - 1 vertices
+    and 2^40 entries, admitted under a budget that claims 2^62 bytes: its 16 GiB
+    of offsets are allocated, its 4 TiB neighbour array cannot be, and no copy
+    or kernel runs (the copies follow the three allocations), so the small
+    host arrays passed are never read."""
+    import ctypes
+    from paper_2507_04420_gb300 import lib
+    from paper_2507_04420_gb300._native import ServerConfig, ServerResult
+    MM_ERR_OOM = 2
+
+    def ptr(t):
+        return ctypes.c_void_p(t.data_ptr())
+
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    cfg = ServerConfig()
+    assert lib.mm_server_default_config(ctypes.byref(cfg)) == 0
+    cfg.memory_bytes = 1 << 62
+    cfg.in_place_max_nnz = 0
+    h = ctypes.c_void_p()
+    assert lib.mm_server_create(ctypes.byref(cfg), ctypes.byref(h)) == 0
+    off = torch.zeros(2, dtype=torch.int64)
+    nb = torch.zeros(4, dtype=torch.int32)
+    mate = torch.zeros(4, dtype=torch.int32)
+    t = ctypes.c_uint64()
+    assert lib.mm_server_submit(h, (1 << 31) - 1, 1 << 40, ptr(off), ptr(nb), ptr(mate), ctypes.byref(t)) == 0
+    res = ServerResult()
+    assert lib.mm_server_wait(h, t.value, 120.0, ctypes.byref(res)) == 0
+    assert res.status == MM_ERR_OOM and res.in_place == 0
+    t2 = ctypes.c_uint64()
+    assert lib.mm_server_submit(h, 1, 0, ptr(off), None, ptr(mate), ctypes.byref(t2)) == MM_ERR_OOM
+    assert lib.mm_server_destroy(h) == MM_ERR_OOM
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0 - (1 << 30), (free0, free1)   # the 16 GiB came back
