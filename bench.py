@@ -658,16 +658,17 @@ def run_ours(args):
         zc_s, zc_mode = time_session(True)
         cp_s, cp_mode = time_session(False)
         # bytes the in-place reads move: every row end (the windows read all of
-        # them) and the neighbour ids the sweep reads (its statistics counter)
+        # them) and the 16-byte id quads the selective walk loads (the
+        # statistics counter of the same decision in an eager run)
         with skp.Graph(h_off, h_nb, check=False, host_mapped=True) as hm:
             hm.skipper(status_bits=args.bits, grain=args.grain, stats=1)
-            ids_read = hm.stats()["entries_read"]
-        read_bytes = 8 * (n + 1) + 4 * ids_read
+            quads = hm.stats()["id_loads_open"]
+        read_bytes = 8 * (n + 1) + 16 * quads
         e2e = {"value": job_gedges(world, nnz, zc_s), "unit": UNIT, "ms_per_step": zc_s * 1e3,
                "h2d_bytes_per_step": read_bytes, "d2h_bytes_per_step": 4 * n, "mode": zc_mode,
                "how": "HostSession.run on pinned host tensors: the kernels read the CSR in place "
-                      "(MM_HOST_MAPPED) -- h2d bytes = all row ends + the neighbour ids the sweep "
-                      "reads (stats counter); mm_skipper; mate -> pinned host; sync",
+                      "(MM_HOST_MAPPED, selective id loads) -- h2d bytes = all row ends + the id "
+                      "quads loaded (stats counter); mm_skipper; mate -> pinned host; sync",
                "copy_path": {"value": job_gedges(world, nnz, cp_s), "unit": UNIT, "ms_per_step": cp_s * 1e3,
                              "h2d_bytes_per_step": 8 * (n + 1) + 4 * nnz, "d2h_bytes_per_step": 4 * n,
                              "mode": cp_mode,

@@ -109,9 +109,26 @@ typedef struct mm_options {
                                 reads.  On a CSR that is not symmetric the result
                                 is in general not maximal.  Serial mode and the
                                 edge-list and multi-graph calls ignore it.  0 = off. */
-    uint32_t reserved32;
+    uint32_t id_loads;       /* when the parallel CSR sweep loads a chunk's neighbour
+                                ids: MM_ID_LOADS_EAGER issues every 128-bit load of
+                                the chunk before the row search (the load overlaps
+                                it; quads whose rows are all known matched are
+                                loaded and dropped); MM_ID_LOADS_SELECTIVE searches
+                                first and loads only quads holding an entry of a
+                                row not known matched (fewer bytes, the load after
+                                the search).  MM_ID_LOADS_AUTO (0): selective for
+                                MM_HOST_MAPPED handles, whose reads cross the host
+                                link, eager otherwise.  The result is a maximal
+                                matching either way.  Statistics instances
+                                (stats = 1), the batched and multi-graph calls
+                                and edge-list handles load eagerly.  Other
+                                values give MM_ERR_ARG. */
     uint64_t reserved[3];
 } mm_options;
+
+#define MM_ID_LOADS_AUTO 0u
+#define MM_ID_LOADS_EAGER 1u
+#define MM_ID_LOADS_SELECTIVE 2u
 
 /* Per-kernel device times of the last call made with options.timing = 1. */
 typedef struct mm_timing {
@@ -146,6 +163,10 @@ typedef struct mm_stats {
                                    RSVD->ACC (line 18); the holder's two are checked
                                    on the word their atomic returns */
     uint64_t illegal_transitions;  /* commits / releases that did not find RSVD (0) */
+    uint64_t id_loads;          /* 128-bit neighbour-id loads (4 ids each) issued */
+    uint64_t id_loads_open;     /* of those, the ones holding an entry of a row not
+                                   known matched: the loads MM_ID_LOADS_SELECTIVE
+                                   issues at the same point of the walk */
 } mm_stats;
 
 /*
@@ -216,7 +237,8 @@ mm_status mm_create_csr(uint64_t n, uint64_t nnz, const int64_t *d_offsets,
  * them in place through the host link -- NVLink-C2C on a Grace-Blackwell
  * node -- so a call moves only what it reads: the sweep's row skip leaves
  * most neighbour ids of a dense graph unread, which a copy of the whole CSR
- * would move all the same.  The state array, the mate output and all scratch
+ * would move all the same, and on such a handle the sweep loads ids
+ * selectively by default (mm_options.id_loads).  The state array, the mate output and all scratch
  * stay in device memory.  The arrays must stay valid and unchanged while the
  * handle is used.  MM_ERR_ARG when the device cannot address an array.
  */

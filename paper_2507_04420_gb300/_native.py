@@ -87,7 +87,7 @@ class Options(ctypes.Structure):
         ("spin_limit", ctypes.c_uint64),
         ("poison_vertex", ctypes.c_uint64),
         ("symmetric", ctypes.c_uint32),
-        ("reserved32", ctypes.c_uint32),
+        ("id_loads", ctypes.c_uint32),
         ("reserved", ctypes.c_uint64 * 3),
     ]
 
@@ -171,6 +171,8 @@ class Stats(ctypes.Structure):
         ("hist", ctypes.c_uint64 * 10),
         ("transitions", ctypes.c_uint64 * 4),
         ("illegal_transitions", ctypes.c_uint64),
+        ("id_loads", ctypes.c_uint64),
+        ("id_loads_open", ctypes.c_uint64),
     ]
 
     def as_dict(self):

@@ -66,6 +66,7 @@ struct mm_graph {
   int num_sms = 0;
   uint64_t n = 0, nnz = 0;            // nnz: stored entries (CSR) or listed edges (edge list)
   bool coo = false;                   // made by mm_create_coo: an edge list, no CSR
+  bool host_mapped = false;           // the input arrays are host memory read in place
   const int64_t* offsets = nullptr;
   const uint32_t* nbrs = nullptr;
   const uint32_t* src = nullptr;      // edge list (coo): edge i = (src[i], dst[i])
@@ -112,7 +113,7 @@ struct Resolved {
   uint32_t grain;
   int block;
   int blocks_per_sm;
-  bool nosync, timing, use_graph, l2_persist, stats, sym;
+  bool nosync, timing, use_graph, l2_persist, stats, sym, sel;
   uint64_t spin_limit, poison;
 };
 
@@ -139,6 +140,8 @@ mm_status resolve(const mm_graph* g, const mm_options* o, Resolved* r) {
   r->l2_persist = o->l2_persist != 0;
   r->stats = o->stats != 0;
   r->sym = o->symmetric != 0;
+  if (o->id_loads > MM_ID_LOADS_SELECTIVE) return fail(MM_ERR_ARG, "id_loads must be 0, 1 or 2 (got %u)", o->id_loads);
+  r->sel = o->id_loads == MM_ID_LOADS_SELECTIVE || (o->id_loads == MM_ID_LOADS_AUTO && g->host_mapped);
   r->spin_limit = o->spin_limit ? o->spin_limit : kDefaultSpin;
   r->poison = o->poison_vertex;
   if (r->poison > g->n) return fail(MM_ERR_ARG, "poison_vertex out of range");
@@ -179,6 +182,7 @@ SweepParams make_params(mm_graph* g, const Resolved& r, uint32_t* d_mate) {
   P.spin_limit = r.spin_limit;
   P.poison = r.poison;
   P.sym = r.sym && !r.serial;
+  P.sel = r.sel && !r.serial;
   return P;
 }
 
@@ -475,6 +479,7 @@ mm_status mm_create_coo(uint64_t n, uint64_t m, const uint32_t* d_src, const uin
   mm_graph* g = nullptr;
   if ((ms = new_handle(n, m, s, &g)) != MM_OK) return ms;
   g->coo = true;
+  g->host_mapped = (flags & MM_HOST_MAPPED) != 0;
   g->src = d_src;
   g->dst = d_dst;
   if (flags & MM_CHECK_CSR) {
@@ -514,6 +519,7 @@ mm_status mm_create_csr(uint64_t n, uint64_t nnz, const int64_t* d_offsets, cons
   if ((ms = new_handle(n, nnz, s, &g)) != MM_OK) return ms;
   g->offsets = d_offsets;
   g->nbrs = d_nbrs;
+  g->host_mapped = (flags & MM_HOST_MAPPED) != 0;
   if ((ms = ensure_part(g, (n + nnz + kDefaultGrain - 1) / kDefaultGrain)) != MM_OK) {
     mm_destroy(g);
     return ms;
@@ -755,6 +761,7 @@ mm_status mm_skipper_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d_
   const uint64_t units = (g->n + g->nnz + r.grain - 1) / r.grain;
   if ((st = ensure_part(g, units)) != MM_OK) return st;
   SweepParams P = make_params(g, r, d_mate);
+  P.sel = 0;  // batched sweeps load ids eagerly (the graph-launched ones share one kernel)
   P.vbase = d_vbase;
   P.num_graphs = num_graphs;
   (void)d_ebase;  // entry ranges follow from offsets[vbase[k]]; kept in the ABI for callers

@@ -54,6 +54,9 @@ struct SweepParams {
   // 1: the CSR is symmetric; an entry (x, y) with y < x is left to row y
   // (selects the kSym kernel instance)
   uint32_t sym;
+  // 1: load only the id quads that hold an entry of a row not known matched
+  // (selects the kSel kernel instance; statistics instances load every quad)
+  uint32_t sel;
 };
 
 // Sweep statistics, kept only by the kStats kernel instances.  A conflict is a
@@ -71,6 +74,8 @@ enum StatSlot : int {
   kStHist,          // 10 bins: 1, 2, 3-4, 5-8, 9-16, 17-32, 33-64, 65-128, 129-256, >256
   kStTrans = kStHist + 10,  // state transitions (Fig. 4): ACC->RSVD, ACC->MCHD, RSVD->MCHD, RSVD->ACC
   kStIllegal = kStTrans + 4,  // commits / releases that found the field not RSVD
+  kStIdLoads,       // 128-bit id loads issued
+  kStIdLoadsOpen,   // of those, quads holding an entry of a row not known matched
   kStCount
 };
 

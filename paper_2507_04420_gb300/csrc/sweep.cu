@@ -78,7 +78,7 @@ __global__ void prepare_kernel(SweepParams P, uint64_t* graph_pairs, uint64_t nu
   }
 }
 
-template <class S, bool kStats = false, bool kSym = false>
+template <class S, bool kStats = false, bool kSym = false, bool kSel = false>
 __global__ void __launch_bounds__(512, 3) sweep_kernel(SweepParams P) {
   const unsigned lane = threadIdx.x & 31u;
   const S s(P);
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(512, 3) sweep_kernel(SweepParams P) {
     const int64_t row0 = P.part[2 * w];
     const int64_t e_begin = P.part[2 * w + 1];
     const int64_t e_end = P.part[2 * w + 3];
-    if (e_begin < e_end) sweep_unit<S, kStats, kSym>(s, P, row0, e_begin, e_end, lane, pol);
+    if (e_begin < e_end) sweep_unit<S, kStats, kSym, kSel>(s, P, row0, e_begin, e_end, lane, pol);
     if ((w & 15) == 0) {  // stop handing out work once an error is recorded
       uint32_t e = 0;
       if (lane == 0) e = ld_relaxed(P.err);
@@ -168,8 +168,17 @@ cudaError_t launch_prepare(const SweepParams& P, int bits, int grid, cudaStream_
 
 cudaError_t launch_sweep(const SweepParams& P, int bits, int grid, int block, cudaStream_t s) {
   if (block > 512 || block < 32 || block % 32) return cudaErrorInvalidValue;
-  // instances: statistics or not, symmetric filter or not
-  if (P.stats && P.sym) {
+  // instances: statistics or not, symmetric filter or not, selective id loads
+  // or not (statistics instances load eagerly)
+  if (P.sel && !P.stats && P.sym) {
+#define L(S, B) (sweep_kernel<S, false, true, true><<<grid, block, 0, s>>>(P), 0)
+    SKP_DISPATCH_STATE(bits, L);
+#undef L
+  } else if (P.sel && !P.stats) {
+#define L(S, B) (sweep_kernel<S, false, false, true><<<grid, block, 0, s>>>(P), 0)
+    SKP_DISPATCH_STATE(bits, L);
+#undef L
+  } else if (P.stats && P.sym) {
 #define L(S, B) (sweep_kernel<S, true, true><<<grid, block, 0, s>>>(P), 0)
     SKP_DISPATCH_STATE(bits, L);
 #undef L

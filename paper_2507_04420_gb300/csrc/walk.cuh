@@ -49,6 +49,20 @@ __device__ __forceinline__ int count_le(int rel, int p) {
   return c;
 }
 
+// Four neighbour ids from entry e0 on (one aligned 128-bit load when all four
+// exist, else the ones below nnz).
+__device__ __forceinline__ void load_quad(const SweepParams& P, int64_t e0, uint64_t pol,
+                                          uint32_t (&y)[4]) {
+  if (e0 + 4 <= (int64_t)P.nnz) {
+    const uint4 q = ld_stream_v4(P.nbrs + e0, pol);
+    y[0] = q.x; y[1] = q.y; y[2] = q.z; y[3] = q.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (e0 + j < (int64_t)P.nnz) y[j] = ld_stream(P.nbrs + e0 + j, pol);
+  }
+}
+
 // One work unit: entries [pos, e_end), the first of which lies in row >= row0.
 //
 // The warp keeps a window of 32 consecutive rows: lane k holds the end offset
@@ -60,7 +74,14 @@ __device__ __forceinline__ int count_le(int rel, int p) {
 // read in chunks of up to 128 (one aligned 128-bit load per lane); the state
 // of the row at the head of each chunk is re-read alongside, so a long row
 // matched by another warp is left after at most one more chunk.
-template <class S, bool kStats = false, bool kSym = false>
+//
+// kSel (selective id loads): a lane loads its quad only after the row search,
+// and only when the quad holds an entry of a row not known matched.  The
+// eager walk issues every load of the chunk first, so that its latency
+// overlaps the search; the selective walk moves fewer bytes (on R-MAT, well
+// under half the quads of a chunk are in rows not known matched), which pays
+// where the bytes cross the host link.
+template <class S, bool kStats = false, bool kSym = false, bool kSel = false>
 __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int64_t row0,
                                            int64_t pos, const int64_t e_end, const unsigned lane,
                                            const uint64_t pol_stream) {
@@ -118,16 +139,7 @@ __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int
     const int p0 = 4 * (int)lane;
     const int64_t e0 = base + p0;
     uint32_t y[4] = {0u, 0u, 0u, 0u};
-    if (p0 < hi_r) {
-      if (e0 + 4 <= (int64_t)P.nnz) {
-        const uint4 q = ld_stream_v4(P.nbrs + e0, pol_stream);
-        y[0] = q.x; y[1] = q.y; y[2] = q.z; y[3] = q.w;
-      } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (e0 + j < (int64_t)P.nnz) y[j] = ld_stream(P.nbrs + e0 + j, pol_stream);
-      }
-    }
+    if (!kSel && p0 < hi_r) load_quad(P, e0, pol_stream, y);
     const uint32_t x1 = (uint32_t)(wbase + k1);
     uint32_t head = 0;
     if (lane == 0) head = s.peek(x1);  // consumed after the row search, so both loads overlap it
@@ -149,6 +161,24 @@ __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int
     uint32_t xs[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) xs[j] = (uint32_t)(wbase + k[j]);
+    if (kSel || kStats) {
+      // does this lane's quad hold an entry of a row not known matched?
+      bool open_quad = false;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int p = p0 + j;
+        open_quad |= p >= lo_r && p < hi_r && !(mchd >> (k[j] & 31) & 1u);
+      }
+      if (kSel && open_quad) load_quad(P, e0, pol_stream, y);
+      if (kStats) {
+        const unsigned issued = __ballot_sync(kFull, p0 < hi_r);
+        const unsigned wanted = __ballot_sync(kFull, open_quad);
+        if (lane == 0) {
+          atomicAdd(P.stats + kStIdLoads, (unsigned long long)__popc(issued));
+          atomicAdd(P.stats + kStIdLoadsOpen, (unsigned long long)__popc(wanted));
+        }
+      }
+    }
 
     // filter (the line-10 read): candidates have both endpoints unmatched.  A
     // row whose snapshot word reads MCHD has its bit in mchd (set when the

@@ -55,8 +55,9 @@ int main(void) {
          offsetof(mm_server_config, opts), offsetof(mm_server_config, reserved),
          sizeof(mm_server_result), offsetof(mm_server_result, verdict),
          offsetof(mm_server_result, done_ns), sizeof(mm_graph_desc));
-  printf("%zu %zu %zu\n", sizeof(mm_stats), offsetof(mm_stats, transitions),
-         offsetof(mm_stats, illegal_transitions));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(mm_stats), offsetof(mm_stats, transitions),
+         offsetof(mm_stats, illegal_transitions), offsetof(mm_stats, id_loads_open),
+         offsetof(mm_options, id_loads), (size_t)MM_ID_LOADS_SELECTIVE);
   return 0;
 }
 """
@@ -73,7 +74,8 @@ int main(void) {
                     O.symmetric.offset, ctypes.sizeof(C), C.opts.offset, C.reserved.offset,
                     ctypes.sizeof(R), R.verdict.offset, R.done_ns.offset, ctypes.sizeof(G),
                     ctypes.sizeof(native.Stats), native.Stats.transitions.offset,
-                    native.Stats.illegal_transitions.offset]
+                    native.Stats.illegal_transitions.offset, native.Stats.id_loads_open.offset,
+                    O.id_loads.offset, 2]
 
 
 def test_default_options_and_argument_errors(native):

@@ -80,8 +80,8 @@ def test_serial_equals_sgmm(skp, name, bits):
 def test_parallel_valid_and_verdicts_identical(skp, name, bits):
     csr = SMALL[name]()
     _, ref_pairs = oracle.sgmm(csr.offsets.numpy(), csr.nbrs.numpy())
-    for grain in (128, 2048):
-        m, p, vr, vd = run(skp, csr, status_bits=bits, grain=grain)
+    for grain, id_loads in ((128, 1), (2048, 1), (128, 2), (2048, 2)):   # eager, selective
+        m, p, vr, vd = run(skp, csr, status_bits=bits, grain=grain, id_loads=id_loads)
         assert_parity(vr, vd)
         assert 2 * len(p) >= len(ref_pairs)
         if name == "star64":
@@ -102,8 +102,8 @@ def test_er_100k_1m(skp, bits):
     m, p, vr, vd = run(skp, csr, status_bits=bits, serial=1)
     assert np.array_equal(m, ref_mate)
     assert_parity(vr, vd)
-    for grain in (256, 2048, 8192):
-        m, p, vr, vd = run(skp, csr, status_bits=bits, grain=grain)
+    for grain, id_loads in ((256, 0), (2048, 0), (8192, 0), (2048, 2), (8192, 2)):
+        m, p, vr, vd = run(skp, csr, status_bits=bits, grain=grain, id_loads=id_loads)
         assert_parity(vr, vd)
         assert 2 * len(p) >= len(ref_pairs)
 
@@ -112,8 +112,9 @@ def test_er_100k_1m(skp, bits):
 @pytest.mark.parametrize("block", [32, 256, 512])
 def test_launch_shapes(skp, bits, block):
     csr = gg.rmat(14, 16, seed=9)
-    for bps in (0, 1):
-        m, p, vr, vd = run(skp, csr, status_bits=bits, block_threads=block, blocks_per_sm=bps)
+    for bps, id_loads in ((0, 1), (1, 1), (0, 2)):
+        m, p, vr, vd = run(skp, csr, status_bits=bits, block_threads=block, blocks_per_sm=bps,
+                           id_loads=id_loads)
         assert_parity(vr, vd)
 
 
@@ -166,8 +167,8 @@ def test_symmetric_option(skp, bits):
     one size); serial mode ignores the option."""
     for name in ("rmat10", "er2k", "grid16x32", "star64", "k3_17", "k9", "disjoint50", "path101"):
         csr = SMALL[name]()
-        for grain in (128, 2048):
-            m, p, vr, vd = run(skp, csr, status_bits=bits, grain=grain, symmetric=1)
+        for grain, id_loads in ((128, 1), (2048, 1), (2048, 2)):
+            m, p, vr, vd = run(skp, csr, status_bits=bits, grain=grain, symmetric=1, id_loads=id_loads)
             assert_parity(vr, vd)
             fixed = {"star64": 1, "k3_17": 3, "k9": 4, "disjoint50": 50}
             if name in fixed:
@@ -177,8 +178,9 @@ def test_symmetric_option(skp, bits):
         assert np.array_equal(m, ref_mate)
     for bits_ in (bits,):
         csr = gg.rmat(18, 16, seed=7)
-        m, p, vr, vd = run(skp, csr, status_bits=bits_, grain=8192, symmetric=1)
-        assert_parity(vr, vd)
+        for id_loads in (1, 2):
+            m, p, vr, vd = run(skp, csr, status_bits=bits_, grain=8192, symmetric=1, id_loads=id_loads)
+            assert_parity(vr, vd)
 
 
 def test_symmetric_option_is_the_callers_promise(skp):
@@ -351,5 +353,27 @@ def test_sweep_statistics(skp, bits):
             assert st["matches"] <= st["attempts"]
             assert 0 < st["entries_read"] <= csr.nnz
             assert st["conflicted_entries"] == sum(st["hist"])
+            # every id read comes from a 128-bit load; the selective walk's loads
+            # are a subset of the eager walk's
+            assert 4 * st["id_loads"] >= st["entries_read"]
+            assert 0 < st["id_loads_open"] <= st["id_loads"]
             assert st["conflicts"] >= st["conflicted_entries"]
             assert (st["max_conflicts"] > 0) == (st["conflicted_entries"] > 0)
+
+
+def test_id_loads_option(skp):
+    """id_loads: 0 (automatic), 1 (eager) and 2 (selective) give maximal
+    matchings with oracle-identical verdicts on a ragged R-MAT; serial mode
+    ignores it; any other value is refused before any device work."""
+    csr = gg.rmat(16, 16, seed=11)
+    for id_loads in (0, 1, 2):
+        m, p, vr, vd = run(skp, csr, grain=2048, id_loads=id_loads)
+        assert_parity(vr, vd)
+    ref_mate, _ = oracle.sgmm(csr.offsets.numpy(), csr.nbrs.numpy())
+    m, p, vr, vd = run(skp, csr, serial=1, id_loads=2)
+    assert np.array_equal(m, ref_mate)
+    d = csr.to("cuda")
+    with skp.Graph(d.offsets, d.nbrs) as h:
+        with pytest.raises(skp.SkipperError) as e:
+            h.skipper(id_loads=3)
+        assert e.value.status == "MM_ERR_ARG"
