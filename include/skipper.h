@@ -120,9 +120,12 @@ typedef struct mm_options {
                                 MM_HOST_MAPPED handles, whose reads cross the host
                                 link, eager otherwise.  The result is a maximal
                                 matching either way.  Statistics instances
-                                (stats = 1), the batched and multi-graph calls
-                                and edge-list handles load eagerly.  Other
-                                values give MM_ERR_ARG. */
+                                (stats = 1), batched calls and edge-list
+                                handles load eagerly; mm_skipper_multi loads
+                                eagerly unless asked for selective loads (the
+                                server asks for them in every launch that reads
+                                a request in place).  Other values give
+                                MM_ERR_ARG. */
     uint64_t reserved[3];
 } mm_options;
 

@@ -103,7 +103,7 @@ __global__ void multi_prepare_kernel(MultiParams M) {
   }
 }
 
-template <class S, bool kWord>
+template <class S, bool kWord, bool kSel = false>
 __global__ void __launch_bounds__(512, 3) multi_sweep_kernel(MultiParams M) {
   const unsigned lane = threadIdx.x & 31u;
   const uint64_t pol = policy_evict_first();
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(512, 3) multi_sweep_kernel(MultiParams M) {
     const int64_t row0 = M.part[2 * w];
     const int64_t e_begin = M.part[2 * w + 1];
     const int64_t e_end = (w + 1 < M.units && M.gid[w + 1] == g) ? M.part[2 * w + 3] : (int64_t)P.nnz;
-    if (e_begin < e_end) sweep_unit(S(P), P, row0, e_begin, e_end, lane, pol);
+    if (e_begin < e_end) sweep_unit<S, false, false, kSel>(S(P), P, row0, e_begin, e_end, lane, pol);
     if ((w & 15) == 0) {
       uint32_t e = 0;
       if (lane == 0) e = ld_relaxed(M.err);
@@ -472,6 +472,8 @@ mm_status mm_skipper_multi(mm_multi* m, uint64_t num_graphs, const mm_graph_desc
   if (grain % 128 || grain > (1u << 24)) return mfail(MM_ERR_ARG, "bad grain");
   const int block = o->block_threads ? (int)o->block_threads : 512;
   if (block < 32 || block > 512 || block % 32) return mfail(MM_ERR_ARG, "bad block_threads");
+  if (o->id_loads > MM_ID_LOADS_SELECTIVE) return mfail(MM_ERR_ARG, "id_loads must be 0, 1 or 2");
+  const bool sel = o->id_loads == MM_ID_LOADS_SELECTIVE;   // automatic: eager
   if (o->timing || o->use_graph || o->poison_vertex || o->l2_persist)
     return mfail(MM_ERR_UNSUPPORTED, "timing, use_graph, poison_vertex and l2_persist are not "
                                      "available in multi-graph calls");
@@ -501,9 +503,15 @@ mm_status mm_skipper_multi(mm_multi* m, uint64_t num_graphs, const mm_graph_desc
       if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     }
     const int grid = m->num_sms * per_sm;
-    if (bits == 32) multi_sweep_kernel<WordState, true><<<grid, block, 0, s>>>(M);
-    else if (bits == 2) multi_sweep_kernel<TwoBitState, false><<<grid, block, 0, s>>>(M);
-    else multi_sweep_kernel<ByteState, false><<<grid, block, 0, s>>>(M);
+    if (sel) {
+      if (bits == 32) multi_sweep_kernel<WordState, true, true><<<grid, block, 0, s>>>(M);
+      else if (bits == 2) multi_sweep_kernel<TwoBitState, false, true><<<grid, block, 0, s>>>(M);
+      else multi_sweep_kernel<ByteState, false, true><<<grid, block, 0, s>>>(M);
+    } else {
+      if (bits == 32) multi_sweep_kernel<WordState, true><<<grid, block, 0, s>>>(M);
+      else if (bits == 2) multi_sweep_kernel<TwoBitState, false><<<grid, block, 0, s>>>(M);
+      else multi_sweep_kernel<ByteState, false><<<grid, block, 0, s>>>(M);
+    }
   }
   MTRY(cudaGetLastError());
   MTRY(cudaMemcpyAsync(m->h_err, M.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));

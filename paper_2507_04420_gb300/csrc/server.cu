@@ -224,6 +224,11 @@ mm_status launch_tick(mm_server* s, std::vector<Req>& staged, std::deque<Tick>& 
   }
   mm_options o = s->cfg.opts;
   o.nosync = 1;
+  // requests read in place cross the host link: selective id loads unless
+  // the configuration fixes the choice
+  bool any_in_place = false;
+  for (const Req& r : staged) any_in_place = any_in_place || r.in_place;
+  if (o.id_loads == MM_ID_LOADS_AUTO && any_in_place) o.id_loads = MM_ID_LOADS_SELECTIVE;
   mm_status ms = mm_skipper_multi(multi, descs.size(), descs.data(), &o, st);
   if (ms != MM_OK) {
     snprintf(s->failure_msg, sizeof s->failure_msg, "mm_skipper_multi: %s", mm_last_error());

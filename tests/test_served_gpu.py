@@ -51,8 +51,8 @@ def test_multi_serial_equals_sgmm_and_parallel_valid(skp, graphs, bits):
         for g, mt in zip(graphs, mates):
             ref, _ = oracle.sgmm(g.offsets.numpy(), g.nbrs.numpy())
             assert np.array_equal(_np(mt), ref)
-        for grain in (128, 2048):
-            m.run(tri, status_bits=bits, grain=grain)
+        for grain, id_loads in ((128, 0), (2048, 0), (128, 2), (2048, 2)):   # eager, selective
+            m.run(tri, status_bits=bits, grain=grain, id_loads=id_loads)
             verdicts = m.validate(tri)
             for g, mt, vd in zip(graphs, mates, verdicts):
                 vr = oracle.check(g.offsets.numpy(), g.nbrs.numpy(), _np(mt))
