@@ -70,6 +70,10 @@ struct mm_server {
   int device = 0;
   cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaStream_t slot_stream[2] = {nullptr, nullptr};
+  // the server's own stream-ordered pool: it keeps freed memory mapped (up to
+  // the budget) instead of returning it at every synchronisation, so a
+  // request's buffers rarely need fresh device pages
+  cudaMemPool_t pool = nullptr;
   mm_multi* slot_multi[2] = {nullptr, nullptr};
   int slots = 2, next_slot = 0;
   std::vector<cudaEvent_t> event_pool;
@@ -177,9 +181,9 @@ void fail_all(mm_server* s, std::deque<Req>& pending, std::vector<Req>& staged,
 // copy path: the request's own device buffers, filled on the copy stream
 mm_status admit_copy(mm_server* s, Req& r) {
   r.own = true;   // whatever of the three is allocated belongs to the request
-  W_TRY(cudaMallocAsync((void**)&r.off, 8 * (r.n + 1), s->h2d));
-  W_TRY(cudaMallocAsync((void**)&r.nb, 4 * (r.nnz ? r.nnz : 1), s->h2d));
-  W_TRY(cudaMallocAsync((void**)&r.mate, 4 * (r.n ? r.n : 1), s->h2d));
+  W_TRY(cudaMallocFromPoolAsync((void**)&r.off, 8 * (r.n + 1), s->pool, s->h2d));
+  W_TRY(cudaMallocFromPoolAsync((void**)&r.nb, 4 * (r.nnz ? r.nnz : 1), s->pool, s->h2d));
+  W_TRY(cudaMallocFromPoolAsync((void**)&r.mate, 4 * (r.n ? r.n : 1), s->pool, s->h2d));
   W_TRY(cudaMemcpyAsync(const_cast<int64_t*>(r.off), r.h_off, 8 * (r.n + 1), cudaMemcpyHostToDevice, s->h2d));
   if (r.nnz)
     W_TRY(cudaMemcpyAsync(const_cast<uint32_t*>(r.nb), r.h_nb, 4 * r.nnz, cudaMemcpyHostToDevice, s->h2d));
@@ -208,7 +212,7 @@ mm_status launch_tick(mm_server* s, std::vector<Req>& staged, std::deque<Tick>& 
     if (r.in_place) arena_n += r.n;
   uint32_t* arena = nullptr;
   if (arena_n) {
-    W_TRY(cudaMallocAsync((void**)&arena, 4 * arena_n, st));
+    W_TRY(cudaMallocFromPoolAsync((void**)&arena, 4 * arena_n, s->pool, st));
     *arena_out = arena;
     uint64_t at = 0;
     for (Req& r : staged)
@@ -440,6 +444,7 @@ mm_status mm_server_create(const mm_server_config* cfg, mm_server** out) {
     }
     if (s->h2d) cudaStreamDestroy(s->h2d);
     if (s->d2h) cudaStreamDestroy(s->d2h);
+    if (s->pool) cudaMemPoolDestroy(s->pool);
     delete s;
     return sfail(st, "mm_server_create: %s", what);
   };
@@ -448,6 +453,19 @@ mm_status mm_server_create(const mm_server_config* cfg, mm_server** out) {
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return bail(MM_ERR_CUDA, "cudaMemGetInfo");
     s->cfg.memory_bytes = free_b > cfg->reserve_bytes ? free_b - cfg->reserve_bytes : 0;
+  }
+  {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = s->device;
+    if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess) {
+      s->pool = nullptr;
+      return bail(MM_ERR_CUDA, "cudaMemPoolCreate");
+    }
+    uint64_t keep = s->cfg.memory_bytes;
+    if (cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess)
+      return bail(MM_ERR_CUDA, "cudaMemPoolSetAttribute");
   }
   if (cudaStreamCreateWithFlags(&s->h2d, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->d2h, cudaStreamNonBlocking) != cudaSuccess)
@@ -557,6 +575,7 @@ mm_status mm_server_destroy(mm_server* s) {
   if (s->h2d) cudaStreamDestroy(s->h2d);
   if (s->d2h) cudaStreamDestroy(s->d2h);
   for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
+  if (s->pool) cudaMemPoolDestroy(s->pool);   // its memory goes back to the device
   char msg[256];
   snprintf(msg, sizeof msg, "%s", s->failure_msg);
   delete s;
