@@ -126,7 +126,18 @@ typedef struct mm_options {
                                 server asks for them in every launch that reads
                                 a request in place).  Other values give
                                 MM_ERR_ARG. */
-    uint64_t reserved[3];
+    uint32_t stage_windows;  /* 1: the parallel CSR sweep of mm_skipper stages each
+                                32-row window (its row ends and state words) in
+                                shared memory with a bulk copy (TMA) issued one
+                                window ahead, instead of loading them when the
+                                window starts.  Used for the 2- and 8-bit layouts
+                                over a 16-byte aligned device CSR without
+                                statistics or selective loads; ignored otherwise.
+                                Off by default: on GB300 it is slower (the sweep
+                                is bound by instruction issue, and the staged
+                                state words are one window old).  0 = off. */
+    uint32_t reserved32;
+    uint64_t reserved[2];
 } mm_options;
 
 #define MM_ID_LOADS_AUTO 0u

@@ -88,7 +88,9 @@ class Options(ctypes.Structure):
         ("poison_vertex", ctypes.c_uint64),
         ("symmetric", ctypes.c_uint32),
         ("id_loads", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint64 * 3),
+        ("stage_windows", ctypes.c_uint32),
+        ("reserved32", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint64 * 2),
     ]
 
 

@@ -113,7 +113,7 @@ struct Resolved {
   uint32_t grain;
   int block;
   int blocks_per_sm;
-  bool nosync, timing, use_graph, l2_persist, stats, sym, sel;
+  bool nosync, timing, use_graph, l2_persist, stats, sym, sel, stage;
   uint64_t spin_limit, poison;
 };
 
@@ -142,6 +142,7 @@ mm_status resolve(const mm_graph* g, const mm_options* o, Resolved* r) {
   r->sym = o->symmetric != 0;
   if (o->id_loads > MM_ID_LOADS_SELECTIVE) return fail(MM_ERR_ARG, "id_loads must be 0, 1 or 2 (got %u)", o->id_loads);
   r->sel = o->id_loads == MM_ID_LOADS_SELECTIVE || (o->id_loads == MM_ID_LOADS_AUTO && g->host_mapped);
+  r->stage = o->stage_windows != 0;
   r->spin_limit = o->spin_limit ? o->spin_limit : kDefaultSpin;
   r->poison = o->poison_vertex;
   if (r->poison > g->n) return fail(MM_ERR_ARG, "poison_vertex out of range");
@@ -183,6 +184,10 @@ SweepParams make_params(mm_graph* g, const Resolved& r, uint32_t* d_mate) {
   P.poison = r.poison;
   P.sym = r.sym && !r.serial;
   P.sel = r.sel && !r.serial;
+  // staged windows: bulk copies want 16-byte aligned device arrays
+  const bool aligned16 = ((reinterpret_cast<uintptr_t>(g->offsets) |
+                           reinterpret_cast<uintptr_t>(P.state)) & 15u) == 0;
+  P.tile = r.stage && !r.serial && !r.word && !g->host_mapped && aligned16;
   return P;
 }
 
@@ -762,6 +767,7 @@ mm_status mm_skipper_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d_
   if ((st = ensure_part(g, units)) != MM_OK) return st;
   SweepParams P = make_params(g, r, d_mate);
   P.sel = 0;  // batched sweeps load ids eagerly (the graph-launched ones share one kernel)
+  P.tile = 0;
   P.vbase = d_vbase;
   P.num_graphs = num_graphs;
   (void)d_ebase;  // entry ranges follow from offsets[vbase[k]]; kept in the ABI for callers

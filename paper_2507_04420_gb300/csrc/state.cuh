@@ -57,6 +57,9 @@ struct SweepParams {
   // 1: load only the id quads that hold an entry of a row not known matched
   // (selects the kSel kernel instance; statistics instances load every quad)
   uint32_t sel;
+  // 1: stage each 32-row window (row ends and state words) in shared memory
+  // with a bulk copy one window ahead (selects the kTile kernel instance)
+  uint32_t tile;
 };
 
 // Sweep statistics, kept only by the kStats kernel instances.  A conflict is a
@@ -125,6 +128,42 @@ __device__ __forceinline__ uint32_t ld_stream(const uint32_t* p, uint64_t policy
                : "=r"(r)
                : "l"(p), "l"(policy));
   return r;
+}
+
+// --- bulk copies into shared memory (the TMA engine) with an mbarrier ---
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// bytes (a multiple of 16) from 16-byte aligned global src to 16-byte aligned shared dst
+__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, uint32_t bytes,
+                                             unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
 }
 
 __device__ __forceinline__ uint64_t policy_evict_first() {
@@ -235,6 +274,7 @@ __host__ __device__ __forceinline__ uint64_t packed_words(uint64_t n, int bits) 
 }
 
 struct WordState {
+  static constexpr uint32_t kPerWord = 1;
   uint32_t* words;
   __device__ explicit WordState(const SweepParams& P) : words(P.state) {}
   __device__ __forceinline__ uint32_t raw(uint32_t v) const { return ld_relaxed(words + v); }

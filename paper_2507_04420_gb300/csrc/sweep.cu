@@ -78,11 +78,13 @@ __global__ void prepare_kernel(SweepParams P, uint64_t* graph_pairs, uint64_t nu
   }
 }
 
-template <class S, bool kStats = false, bool kSym = false, bool kSel = false>
+template <class S, bool kStats = false, bool kSym = false, bool kSel = false, bool kTile = false>
 __global__ void __launch_bounds__(512, 3) sweep_kernel(SweepParams P) {
   const unsigned lane = threadIdx.x & 31u;
   const S s(P);
   const uint64_t pol = policy_evict_first();
+  uint32_t phase = 0;   // parity of the warp's tile barrier (kTile)
+  if (kTile) init_window_tile(lane);
   for (;;) {
     unsigned long long w = 0;
     if (lane == 0) w = atomicAdd(P.work, 1ull);
@@ -91,7 +93,8 @@ __global__ void __launch_bounds__(512, 3) sweep_kernel(SweepParams P) {
     const int64_t row0 = P.part[2 * w];
     const int64_t e_begin = P.part[2 * w + 1];
     const int64_t e_end = P.part[2 * w + 3];
-    if (e_begin < e_end) sweep_unit<S, kStats, kSym, kSel>(s, P, row0, e_begin, e_end, lane, pol);
+    if (e_begin < e_end)
+      sweep_unit<S, kStats, kSym, kSel, kTile>(s, P, row0, e_begin, e_end, lane, pol, &phase);
     if ((w & 15) == 0) {  // stop handing out work once an error is recorded
       uint32_t e = 0;
       if (lane == 0) e = ld_relaxed(P.err);
@@ -148,6 +151,8 @@ __global__ void graph_pairs_kernel(const uint32_t* __restrict__ mate,
 // run F with the state type for `bits` (2, 8 or 32)
 #define SKP_DISPATCH_STATE(bits, F) \
   ((bits) == 32 ? F(WordState, 32) : (bits) == 2 ? F(TwoBitState, 2) : F(ByteState, 8))
+// the same for the packed layouts only (2 or 8)
+#define SKP_DISPATCH_PACKED(bits, F) ((bits) == 2 ? F(TwoBitState, 2) : F(ByteState, 8))
 
 int sweep_blocks_per_sm(int bits, int block_threads) {
   int b = 0;
@@ -169,8 +174,14 @@ cudaError_t launch_prepare(const SweepParams& P, int bits, int grid, cudaStream_
 cudaError_t launch_sweep(const SweepParams& P, int bits, int grid, int block, cudaStream_t s) {
   if (block > 512 || block < 32 || block % 32) return cudaErrorInvalidValue;
   // instances: statistics or not, symmetric filter or not, selective id loads
-  // or not (statistics instances load eagerly)
-  if (P.sel && !P.stats && P.sym) {
+  // or not (statistics instances load eagerly), staged windows or not (the
+  // host side asks for them only for packed states over an aligned device CSR)
+  if (P.tile && !P.stats && !P.sel && bits != 32) {
+#define L(S, B) (P.sym ? (sweep_kernel<S, false, true, false, true><<<grid, block, 0, s>>>(P), 0) \
+                       : (sweep_kernel<S, false, false, false, true><<<grid, block, 0, s>>>(P), 0))
+    SKP_DISPATCH_PACKED(bits, L);
+#undef L
+  } else if (P.sel && !P.stats && P.sym) {
 #define L(S, B) (sweep_kernel<S, false, true, true><<<grid, block, 0, s>>>(P), 0)
     SKP_DISPATCH_STATE(bits, L);
 #undef L

@@ -63,6 +63,37 @@ __device__ __forceinline__ void load_quad(const SweepParams& P, int64_t e0, uint
   }
 }
 
+// Shared-memory tile of one 32-row window (kTile instances, opt-in), filled
+// by one bulk copy (TMA, cp.async.bulk with an mbarrier) while the warp still
+// works on the window before it: the window's row ends (34 int64 from an even
+// index, 272 bytes) and the state words of its rows (12 words from a multiple
+// of 4, 48 bytes).  Both copies start 16-byte aligned (the host enables the
+// instances only for 16-byte aligned arrays in device memory) and stay inside
+// their arrays (n + 1 row ends, ceil(n / per word) state words); a window for
+// which they would not is loaded directly.  The state words are a snapshot one
+// window old: a row matched since then reads as unmatched, which costs an
+// extra filter read, never a wrong result (MCHD is absorbing, and every
+// transition is a CAS on the current word).  Every wait on the barrier is
+// bounded.
+struct alignas(16) WindowTile {
+  int64_t ends[36];
+  uint32_t st[16];
+  unsigned long long bar;
+  unsigned long long pad;
+};
+constexpr uint32_t kTileEnds = 34, kTileWords = 12;
+constexpr uint32_t kTileBytes = kTileEnds * 8 + kTileWords * 4;
+__shared__ WindowTile g_window_tiles[16];       // one per warp of a block of <= 512 threads
+
+// the warp's tile barrier (one arrival per copy); once per warp before its first unit
+__device__ __forceinline__ void init_window_tile(unsigned lane) {
+  if (lane == 0) {
+    mbar_init(&g_window_tiles[threadIdx.x >> 5].bar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+}
+
 // One work unit: entries [pos, e_end), the first of which lies in row >= row0.
 //
 // The warp keeps a window of 32 consecutive rows: lane k holds the end offset
@@ -75,41 +106,89 @@ __device__ __forceinline__ void load_quad(const SweepParams& P, int64_t e0, uint
 // of the row at the head of each chunk is re-read alongside, so a long row
 // matched by another warp is left after at most one more chunk.
 //
+// kTile: windows come from the warp's shared-memory tile (WindowTile above).
+//
 // kSel (selective id loads): a lane loads its quad only after the row search,
 // and only when the quad holds an entry of a row not known matched.  The
 // eager walk issues every load of the chunk first, so that its latency
 // overlaps the search; the selective walk moves fewer bytes (on R-MAT, well
 // under half the quads of a chunk are in rows not known matched), which pays
 // where the bytes cross the host link.
-template <class S, bool kStats = false, bool kSym = false, bool kSel = false>
+template <class S, bool kStats = false, bool kSym = false, bool kSel = false, bool kTile = false>
 __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int64_t row0,
                                            int64_t pos, const int64_t e_end, const unsigned lane,
-                                           const uint64_t pol_stream) {
+                                           const uint64_t pol_stream, uint32_t* phase = nullptr) {
   const uint32_t n32 = (uint32_t)P.n;
   int64_t wbase = row0;
   int64_t my_end;
   uint32_t my_st;
   unsigned mchd;
+  bool pending = false;                         // a copy of the next window's tile is in flight
+  auto tile = [&]() { return &g_window_tiles[threadIdx.x >> 5]; };
+  auto t_s = [&](int64_t w) { return (w + 1) & ~(int64_t)1; };
+  auto t_sw = [&](int64_t w) { return (w / (int64_t)S::kPerWord) & ~(int64_t)3; };
+  auto issue_next = [&](int64_t w) {
+    if (!kTile) return;
+    const int64_t sidx = t_s(w), sw = t_sw(w);
+    // both copies stay inside their arrays: n + 1 row offsets, ceil(n / per word) state words
+    if (sidx + (int64_t)kTileEnds > (int64_t)P.n + 1 ||
+        sw + (int64_t)kTileWords > (int64_t)((P.n + S::kPerWord - 1) / S::kPerWord))
+      return;
+    if (lane == 0) {
+      fence_proxy_async_smem();   // this warp's reads of the tile come before the copy's writes
+      mbar_expect_tx(&tile()->bar, kTileBytes);
+      bulk_to_smem(tile()->ends, P.offsets + sidx, kTileEnds * 8, &tile()->bar);
+      bulk_to_smem(tile()->st, P.state + sw, kTileWords * 4, &tile()->bar);
+    }
+    pending = true;
+  };
+  // bounded wait for the copy in flight; false when it ran past the limit
+  auto wait_tile = [&]() -> bool {
+    for (uint32_t i = 0; i < (1u << 22); ++i)
+      if (mbar_try_wait(&tile()->bar, *phase)) {
+        *phase ^= 1u;
+        pending = false;
+        return true;
+      }
+    return false;
+  };
   {
     const int64_t r = wbase + lane;
     const bool in = r < (int64_t)P.n;
     my_end = in ? __ldg(P.offsets + r + 1) : INT64_MAX;
     my_st = in ? s.peek((uint32_t)r) : 0u;
     mchd = __ballot_sync(kFull, !in || S::matched(my_st, (uint32_t)r));  // rows past n hold no entries
+    issue_next(wbase + 32);
   }
   while (pos < e_end) {
     // rows of the window with entries at or after pos that are not known matched
     const unsigned open = __ballot_sync(kFull, my_end > pos) & ~mchd;
     if (open == 0u) {  // the window is exhausted: continue after its last row
       const int64_t win_end = __shfl_sync(kFull, my_end, 31);
-      if (win_end >= e_end) return;
+      if (win_end >= e_end) break;
       if (win_end > pos) pos = win_end;
       wbase += 32;
       const int64_t r = wbase + lane;
       const bool in = r < (int64_t)P.n;
-      my_end = in ? __ldg(P.offsets + r + 1) : INT64_MAX;
-      my_st = in ? s.peek((uint32_t)r) : 0u;
+      bool from_tile = false;
+      if (kTile && pending) {
+        from_tile = wait_tile();
+        if (!from_tile) {            // the copy did not land: stop, after a last bounded wait
+          if (lane == 0) atomicOr(P.err, kErrTimeout);
+          wait_tile();
+          return;
+        }
+      }
+      if (from_tile) {
+        my_end = in ? tile()->ends[wbase + 1 + lane - t_s(wbase)] : INT64_MAX;
+        my_st = in ? tile()->st[(r / (int64_t)S::kPerWord) - t_sw(wbase)] : 0u;
+        __syncwarp();
+      } else {
+        my_end = in ? __ldg(P.offsets + r + 1) : INT64_MAX;
+        my_st = in ? s.peek((uint32_t)r) : 0u;
+      }
       mchd = __ballot_sync(kFull, !in || S::matched(my_st, (uint32_t)r));
+      issue_next(wbase + 32);
       if (kStats && lane == 0) atomicAdd(P.stats + kStWindows, 1ull);
       continue;
     }
@@ -118,7 +197,7 @@ __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int
       const int64_t st = __shfl_sync(kFull, my_end, k1 - 1);
       if (st > pos) pos = st;
     }
-    if (pos >= e_end) return;
+    if (pos >= e_end) break;
     const int64_t win_end = __shfl_sync(kFull, my_end, 31);
     const int64_t base = pos & ~(int64_t)3;
     int64_t cend = base + 128;
@@ -227,6 +306,10 @@ __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int
         if (done >> (k[jj] & 31) & 1u) cand &= ~(1u << jj);
     }
     pos = cend;
+  }
+  if (kTile && pending && !wait_tile()) {   // the tile is reused by the next unit
+    if (lane == 0) atomicOr(P.err, kErrTimeout);
+    wait_tile();
   }
 }
 

@@ -58,6 +58,7 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(mm_stats), offsetof(mm_stats, transitions),
          offsetof(mm_stats, illegal_transitions), offsetof(mm_stats, id_loads_open),
          offsetof(mm_options, id_loads), (size_t)MM_ID_LOADS_SELECTIVE);
+  printf("%zu %zu\n", offsetof(mm_options, stage_windows), offsetof(mm_options, reserved));
   return 0;
 }
 """
@@ -75,7 +76,7 @@ int main(void) {
                     ctypes.sizeof(R), R.verdict.offset, R.done_ns.offset, ctypes.sizeof(G),
                     ctypes.sizeof(native.Stats), native.Stats.transitions.offset,
                     native.Stats.illegal_transitions.offset, native.Stats.id_loads_open.offset,
-                    O.id_loads.offset, 2]
+                    O.id_loads.offset, 2, O.stage_windows.offset, O.reserved.offset]
 
 
 def test_default_options_and_argument_errors(native):

@@ -377,3 +377,41 @@ def test_id_loads_option(skp):
         with pytest.raises(skp.SkipperError) as e:
             h.skipper(id_loads=3)
         assert e.value.status == "MM_ERR_ARG"
+
+
+@pytest.mark.parametrize("bits", [2, 8])
+def test_stage_windows_option(skp, bits):
+    """stage_windows=1 (windows staged in shared memory by bulk copies one
+    window ahead): maximal matchings with oracle-identical verdicts on ragged
+    sizes, long runs of empty rows, one huge row and windows at the end of the
+    arrays, with and without the symmetric filter; a CSR whose offsets are only
+    8-byte aligned runs the unstaged walk; serial mode ignores the option."""
+    graphs = [gg.rmat(14, 16, seed=21), gg.rmat(12, 4, seed=22), gg.star(5000), gg.grid(33, 47),
+              gg.erdos_renyi(4099, 20000, seed=23), SMALL["path101"](), SMALL["fig1"]()]
+    n = 3000
+    rows = [[] for _ in range(n)]
+    for x in range(0, n, 97):                       # short rows between long runs of empty rows
+        for y in (x + 1, x + 45, x + 300):
+            if y < n:
+                rows[x].append(y)
+                rows[y].append(x)
+    graphs.append(_manual(n, [sorted(r) for r in rows]))
+    for csr in graphs:
+        for grain, sym in ((128, 0), (2048, 0), (8192, 0), (2048, 1)):
+            m, p, vr, vd = run(skp, csr, status_bits=bits, grain=grain, symmetric=sym, stage_windows=1)
+            assert_parity(vr, vd)
+        ref_mate, _ = oracle.sgmm(csr.offsets.numpy(), csr.nbrs.numpy())
+        m, p, vr, vd = run(skp, csr, status_bits=bits, serial=1, stage_windows=1)
+        assert np.array_equal(m, ref_mate)
+    # offsets 8-byte but not 16-byte aligned: the same call, unstaged
+    csr = gg.rmat(13, 16, seed=24)
+    big = torch.zeros(csr.n + 2, dtype=torch.int64, device="cuda")
+    off = big[1:]
+    off.copy_(csr.offsets.cuda())
+    assert off.data_ptr() % 16 == 8
+    nb = csr.nbrs.cuda()
+    with skp.Graph(off, nb) as h:
+        mate = h.skipper(status_bits=bits, stage_windows=1)
+        vd = h.validate(mate)
+    vr = oracle.check(csr.offsets.numpy(), csr.nbrs.numpy(), _np(mate))
+    assert_parity(vr, vd)
