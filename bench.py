@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--bits", type=int, default=8, choices=[2, 8, 32])
     ap.add_argument("--grain", type=int, default=8192)
     ap.add_argument("--block", type=int, default=512)
+    ap.add_argument("--stage-windows", action="store_true",
+                    help="mm_options.stage_windows = 1 for the timed sweep (opt-in TMA window tiles)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="approximate host seconds for the oracle sample")
@@ -545,13 +547,15 @@ def run_ours(args):
     g = make_graph(args, "cuda")
     n, nnz = g.n, g.nnz
     cfg = workload_config(args, g)
+    stage = 1 if args.stage_windows else 0
     opts = skp.options(status_bits=args.bits, grain=args.grain, block_threads=args.block,
-                       nosync=1, timing=1)
+                       nosync=1, timing=1, stage_windows=stage)
     mate = torch.empty(n, dtype=torch.int32, device="cuda")
     h = skp.Graph(g.offsets, g.nbrs, check=True)
 
     # one checked run before timing: the device checker must accept it
-    h.skipper(mate=mate, status_bits=args.bits, grain=args.grain, block_threads=args.block)
+    h.skipper(mate=mate, status_bits=args.bits, grain=args.grain, block_threads=args.block,
+              stage_windows=stage)
     verdict = h.validate(mate)
     if verdict.flags != 0:
         raise SystemExit(f"invalid matching: {verdict.as_dict()}")
@@ -595,7 +599,10 @@ def run_ours(args):
     achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9
     s = {2: 0.25, 8: 1.0, 32: 4.0}[args.bits]   # state bytes per vertex
     step_bytes = int(8 * (n + 1) + 4 * nnz + s * n + (4 * n if args.bits != 32 else 0))
-    traffic = ncu_traffic(cfg["workload"], args.bits)
+    # the committed counters are the default instance's
+    traffic = None if args.stage_windows else ncu_traffic(cfg["workload"], args.bits)
+    if args.stage_windows:
+        cfg["stage_windows"] = 1
 
     # the same graph with mm_options.symmetric = 1 (the CSR is symmetric by
     # construction): each edge tested once, from its lower endpoint's row
