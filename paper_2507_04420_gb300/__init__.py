@@ -104,7 +104,8 @@ class Graph:
                  host_mapped: bool = False):
         if host_mapped:
             _need_pinned(offsets, "offsets", (torch.int64,))
-            _need_pinned(nbrs, "nbrs", _U32)
+            if nbrs.numel():   # an empty array is never read
+                _need_pinned(nbrs, "nbrs", _U32)
             self.device = torch.device("cuda", torch.cuda.current_device())
         else:
             _need(offsets, "offsets", (torch.int64,))

@@ -415,3 +415,52 @@ def test_stage_windows_option(skp, bits):
         vd = h.validate(mate)
     vr = oracle.check(csr.offsets.numpy(), csr.nbrs.numpy(), _np(mate))
     assert_parity(vr, vd)
+
+
+def test_zero_vertex_graphs(skp):
+    """n = 0 (offsets = [0], no entries) through every entry point: the pass,
+    the pair list, the checker and the census on a CSR handle; an empty edge
+    list; a multi-graph launch with an empty graph between two others; a
+    request to the server; the host session; the allocation-free call."""
+    import ctypes
+    off = torch.zeros(1, dtype=torch.int64, device="cuda")
+    nb = torch.zeros(0, dtype=torch.int32, device="cuda")
+    for bits in (2, 8, 32):
+        with skp.Graph(off, nb) as h:
+            for kw in ({}, {"serial": 1}, {"symmetric": 1}, {"id_loads": 2}, {"stage_windows": 1}):
+                mate, pairs, cnt = h.skipper(pairs=True, status_bits=bits, **kw)
+                assert mate.numel() == 0 and int(cnt.item()) == 0
+            v = h.validate(mate)
+            assert v.flags == 0 and v.n_pairs == 0
+            assert h.state_census() == {"acc": 0, "rsvd": 0, "mchd": 0, "other": 0}
+        with skp.EdgeList(0, nb, nb) as h:
+            assert h.skipper(status_bits=bits).numel() == 0
+            assert h.skipper(status_bits=bits, serial=1).numel() == 0
+            assert h.validate(torch.zeros(0, dtype=torch.int32, device="cuda")).flags == 0
+    a, b = gg.path(9).to("cuda"), gg.star(20).to("cuda")
+    mates = [torch.empty(9, dtype=torch.int32, device="cuda"), torch.empty(0, dtype=torch.int32, device="cuda"),
+             torch.empty(21, dtype=torch.int32, device="cuda")]
+    tri = [(a.offsets, a.nbrs, mates[0]), (off, nb, mates[1]), (b.offsets, b.nbrs, mates[2])]
+    m = skp.Multi()
+    try:
+        m.run(tri)
+        vs = m.validate(tri)
+        assert [v.flags for v in vs] == [0, 0, 0] and vs[1].n_pairs == 0 and vs[2].n_pairs == 1
+    finally:
+        m.close()
+    from paper_2507_04420_gb300.server import Server
+    srv = Server(serial=True, status_bits=8)
+    r = srv.submit(torch.zeros(1, dtype=torch.int64).pin_memory(), torch.zeros(0, dtype=torch.int32))
+    assert r.wait(60) and r.error is None and r.verdict.flags == 0 and r.mate.numel() == 0
+    srv.close()
+    sess = skp.HostSession(4, 4)
+    try:
+        for zc in (True, False):
+            sess.zero_copy = zc
+            out = sess.run(torch.zeros(1, dtype=torch.int64).pin_memory(), torch.zeros(0, dtype=torch.int32))
+            assert out.numel() == 0
+    finally:
+        sess.close()
+    o = skp.options()
+    rc = skp.lib.mm_skipper_static(0, 0, ctypes.c_void_p(off.data_ptr()), None, None, ctypes.byref(o), None)
+    assert rc == 0, skp.lib.mm_last_error()
