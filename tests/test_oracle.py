@@ -168,6 +168,35 @@ def test_exhaustive_six_vertices():
         assert oracle.check(off, nb, m).flags == 0
 
 
+def test_sampled_seven_vertices():
+    """Seeded random graphs on 7 vertices (random edge subsets of the 21 pairs,
+    rows in random stored order): SGMM's result is maximal and at least half a
+    maximum matching; every matching of the graph is accepted by the checker
+    exactly when it is maximal."""
+    rng = random.Random(17)
+    n = 7
+    pairs = [(a, b) for a in range(n) for b in range(a + 1, n)]
+    for t in range(1500):
+        adj = [[] for _ in range(n)]
+        for a, b in pairs:
+            if rng.random() < rng.choice((0.2, 0.45, 0.7)):
+                adj[a].append(b)
+                adj[b].append(a)
+        for row in adj:
+            rng.shuffle(row)
+        off, nb = brute.csr_from_adj(n, adj)
+        edges = brute.undirected_edges(off, nb)
+        m, p = oracle.sgmm(off, nb)
+        out = [frozenset((int(a), int(b))) for a, b in p.tolist()]
+        assert brute.is_maximal(edges, out)
+        assert 2 * len(out) >= brute.maximum_matching_size(edges)
+        assert oracle.check(off, nb, m, p).flags == 0
+        if t % 10 == 0:
+            for mt in brute.all_matchings(edges):
+                v = oracle.check(off, nb, np.array(brute.mate_of(n, mt), dtype=np.uint32))
+                assert (v.flags == 0) == brute.is_maximal(edges, mt)
+
+
 @pytest.mark.parametrize("n", [3, 4])
 def test_checker_accepts_exactly_the_maximal_matchings(n):
     """Every mate array over {NONE, 0..n-1} on every graph: accepted iff Section II-B holds."""
