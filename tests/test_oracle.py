@@ -116,6 +116,24 @@ def test_self_loops_and_stored_order():
     assert p.tolist() == [[0, 2]]
 
 
+def test_checker_ignores_self_loops():
+    """A loop is not an edge a matching can cover (Algorithm 1 lines 6-7 skip
+    it): an unmatched vertex whose only entry is a loop leaves nothing
+    uncovered, while a real edge between two unmatched vertices is reported."""
+    # 0 - 1 matched; vertex 2 has only a loop; vertex 3 a loop and the edge 3-4
+    off = [0, 1, 2, 3, 5, 6]
+    nb = [1, 0, 2, 3, 4, 3]
+    mate = np.array([1, 0, NONE, 4, 3], dtype=np.uint32)
+    v = oracle.check(off, nb, mate)
+    assert v.flags == 0 and v.n_uncovered == 0 and v.n_pairs == 2
+    mate = np.array([1, 0, NONE, NONE, NONE], dtype=np.uint32)
+    v = oracle.check(off, nb, mate)
+    assert v.flags == oracle.V_UNCOVERED and v.n_uncovered == 2   # entries 3->4 and 4->3
+    m, _ = oracle.sgmm(off, nb)
+    assert m.tolist() == [1, 0, NONE, 4, 3]
+    assert oracle.check(off, nb, m).flags == 0
+
+
 def test_sgmm_equals_edge_walk_random():
     rng = random.Random(7)
     for _ in range(300):
