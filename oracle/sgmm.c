@@ -2,7 +2,7 @@
  * oracle/sgmm.c -- TEST INFRASTRUCTURE ONLY.
  *
  * Sequential Greedy Maximal Matching (SGMM) over a CSR graph, as the paper
- * defines it in Section II-B ("Maximal Matching"): one thread walks the
+ * defines it in Section II-B (its maximal-matching background): one thread walks the
  * edges; an edge whose two endpoints are both unmarked is taken, and both
  * endpoints are marked.  In CSR order, once the source vertex of a row is
  * marked the rest of that row cannot yield a match, so the row is left
@@ -13,7 +13,7 @@
  * shares no code, header or constant with the CUDA library.  Only tests/,
  * __graft_entry__.smoke() and bench.py's CPU-baseline leg may call it.
  *
- * Edge order (a reading; the paper only says "iterates over edges"): rows
+ * Edge order (a reading; the paper fixes no order beyond walking the edges): rows
  * in ascending vertex id, neighbours in stored order; the first unmarked
  * neighbour wins.
  *
