@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-edge-list", action="store_true")
+    ap.add_argument("--no-side-graphs", action="store_true",
+                    help="skip the uniform and high-skew graphs of the headline's size")
+    ap.add_argument("--side-steps", type=int, default=10)
     ap.add_argument("--served-in-place-max-nnz", type=int, default=1 << 20)
     ap.add_argument("--symmetric-steps", type=int, default=50)
     ap.add_argument("--edge-list-steps", type=int, default=20)
@@ -365,6 +368,99 @@ def run_batched(args, skp):
                plain_gedges_s=csr.nnz / (pct(lat, 50) * 1e-3) / 1e9,
                plain_how="one mm_skipper call per graph (nosync, 2 launches each), then one status read per graph",
                speedup_vs_plain=pct(lat, 50) / out["p50_ms"])
+    return out
+
+
+# ----------------------------------------------------------------------------
+# the other scale-27 graphs: uniform and high-skew R-MAT, every state layout
+# ----------------------------------------------------------------------------
+def time_sweep(h, mate, opts, steps, warmup):
+    """Device time per call and mean init / sweep kernel times of `steps`
+    back-to-back calls (CUDA events on the launching stream)."""
+    import torch
+    for _ in range(max(3, warmup)):
+        h.skipper(mate=mate, opts=opts)
+    h.sync()
+    h.timing_history()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        h.skipper(mate=mate, opts=opts)
+    e1.record()
+    torch.cuda.synchronize()
+    h.sync()
+    hist = h.timing_history(256)
+    return (e0.elapsed_time(e1) / steps, statistics.mean(t["sweep_ms"] for t in hist),
+            statistics.mean(t["init_ms"] for t in hist))
+
+
+def run_side_graphs(args, skp, m_headline):
+    """Config C3's companions of the headline graph: a uniform random graph with
+    the same n and edge draws, and a high-skew R-MAT (a = .7, b = c = d = .1),
+    each timed in the byte, 2-bit and 32-bit state layouts (and the 2-bit
+    layout with symmetric = 1), with the same roofline arithmetic as the
+    headline line."""
+    import graphgen as gg
+    import torch
+    scale, ef = args.scale, args.edge_factor
+    n = 1 << scale
+    chunks = (16 << max(0, scale - 27)) if scale >= 26 else 1
+    peak, peak_kind = measured_peaks()
+    gens = {
+        f"uniform{scale}": (lambda: gg.uniform(n, m_headline, seed=args.seed, device="cuda", chunks=chunks),
+                            f"{m_headline} uniform random pairs on 2^{scale} vertices (the headline R-MAT's n "
+                            "and undirected m), loops and repeats dropped, symmetrised"),
+        f"rmat{scale}_skew": (lambda: gg.rmat(scale, ef, 0.7, 0.1, 0.1, seed=args.seed, device="cuda",
+                                              chunks=chunks),
+                              f"R-MAT scale {scale}, edge factor {ef}, a/b/c/d=.7/.1/.1/.1, ids permuted, "
+                              "symmetrised, deduplicated"),
+    }
+    out = {}
+    for name, (gen, desc) in gens.items():
+        t = time.time()
+        g = gen()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        log(f"{name}: n={g.n} nnz={g.nnz} generated in {time.time() - t:.1f}s")
+        sweep_bytes = 8 * (g.n + 1) + 4 * g.nnz
+        res = {"workload": desc, "n": g.n, "nnz": g.nnz, "grain": args.grain, "block_threads": args.block,
+               "l2": "inputs larger than L2 (CSR %.1f GB); no flush" % (sweep_bytes / 1e9), "layouts": {}}
+        mate = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        with skp.Graph(g.offsets, g.nbrs, check=True) as h:
+            for bits, sym in ((8, 0), (2, 0), (32, 0), (2, 1)):
+                o = skp.options(status_bits=bits, grain=args.grain, block_threads=args.block, nosync=1,
+                                timing=1, symmetric=sym)
+                ms, sweep_ms, init_ms = time_sweep(h, mate, o, args.side_steps, args.warmup)
+                v = h.validate(mate)
+                if v.flags != 0:
+                    raise SystemExit(f"invalid matching on {name} (bits {bits}): {v.as_dict()}")
+                s = {2: 0.25, 8: 1.0, 32: 4.0}[bits]
+                step_bytes = int(8 * (g.n + 1) + 4 * g.nnz + s * g.n + (4 * g.n if bits != 32 else 0))
+                achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9
+                res["layouts"][f"u{bits}" + ("_symmetric" if sym else "")] = {
+                    "ms_per_step": ms, "sweep_ms": sweep_ms, "init_ms": init_ms,
+                    "value": g.nnz / (ms * 1e-3) / 1e9, "unit": UNIT,
+                    "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                 "frac": achieved / peak,
+                                 "traffic": None if sym else ncu_traffic(name, bits),
+                                 "bytes_per_launch": sweep_bytes,
+                                 "kernel": f"sweep_kernel<{ {2: 'TwoBit', 8: 'Byte', 32: 'Word'}[bits]}State>",
+                                 "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
+                                 "step_bytes_alg": step_bytes,
+                                 "step_frac": step_bytes / (ms * 1e-3) / 1e9 / peak},
+                    "verdict": {"flags": v.flags, "n_pairs": v.n_pairs}}
+            h.skipper(mate=mate, status_bits=8, grain=args.grain, block_threads=args.block, stats=1)
+            st = h.stats()
+            res["stats_u8"] = {k: st[k] for k in ("entries_read", "windows", "chunks", "attempts", "matches",
+                                                   "conflicts", "id_loads", "id_loads_open")}
+            res["stats_u8"]["ids_read_frac"] = st["entries_read"] / max(1, g.nnz)
+        best = max(res["layouts"].items(), key=lambda kv: kv[1]["value"])
+        res["best_layout"] = best[0]
+        out[name] = res
+        del g, mate
+        torch.cuda.empty_cache()
     return out
 
 
@@ -745,6 +841,9 @@ def run_ours(args):
     h.close()
     del g, h_off, h_nb
     torch.cuda.empty_cache()
+    side = None
+    if not args.no_side_graphs:
+        side = run_side_graphs(args, skp, nnz // 2)
     edge_list = None
     if not args.no_edge_list:
         edge_list = run_edge_list(args, skp)
@@ -782,6 +881,7 @@ def run_ours(args):
         "kernel_ms": {"init": init_ms, "sweep": sweep_ms},
         "verdict": {"flags": v_end.flags, "n_pairs": v_end.n_pairs},
         "symmetric_option": symmetric,
+        "side_graphs": side,
         "edge_list": edge_list,
         "batched": batched,
         "served": served,

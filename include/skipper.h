@@ -441,16 +441,22 @@ mm_status mm_destroy(mm_graph *g);
  * Limits: n <= MM_STATIC_MAX_VERTICES (larger graphs return MM_ERR_ARG, with
  * the reason in mm_last_error()); the grain is raised when needed so that the
  * partition fits the fixed table.  Options: status_bits 0 or 8, serial, grain,
- * block_threads, blocks_per_sm, spin_limit, poison_vertex; timing, use_graph,
- * nosync and l2_persist give MM_ERR_UNSUPPORTED.  The call waits for its work
- * and returns MM_OK, MM_ERR_TIMEOUT, MM_ERR_BAD_GRAPH, MM_ERR_ARG or
- * MM_ERR_CUDA.
+ * block_threads, blocks_per_sm, spin_limit, poison_vertex, id_loads AUTO or
+ * EAGER.  The options that need a handle's own memory -- timing, use_graph,
+ * nosync, l2_persist, stats, stage_windows, symmetric and id_loads SELECTIVE
+ * -- give MM_ERR_UNSUPPORTED; nothing is ignored silently.  The call waits for
+ * its work and returns MM_OK, MM_ERR_TIMEOUT, MM_ERR_BAD_GRAPH, MM_ERR_ARG,
+ * MM_ERR_UNSUPPORTED or MM_ERR_CUDA, with the reason of every failure in
+ * mm_last_error().
  *
- * The first call on a device looks up the array's device address on that
- * device (make it before any stream capture).  All calls share the one array:
- * each call clears what must start at zero, and calls whose work overlaps on
- * the GPU (two host threads, two streams) race on it and must be serialised
- * by the caller.
+ * Every call looks up the array's address in the calling thread's current
+ * context, so the call stays correct after cudaDeviceReset and in a context
+ * that is not the device's primary one (each context holds its own copy of
+ * the array).  The first call in a context loads the library's device code
+ * there: make it before any stream capture.  All calls in one context share
+ * the one array: each call clears what must start at zero, and calls whose
+ * work overlaps on the GPU (two host threads, two streams) race on it and must
+ * be serialised by the caller.
  */
 #define MM_STATIC_MAX_VERTICES 7864064ull
 mm_status mm_skipper_static(uint64_t n, uint64_t nnz, const int64_t *d_offsets,

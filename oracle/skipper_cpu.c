@@ -18,7 +18,7 @@
  *     (lines 13-16); if u is not MCHD afterwards it is released to ACC
  *     (lines 17-18).  u is held exclusively while RSVD, so lines 15 and 18
  *     are plain (release) stores.
- *   * scheduling (Section IV-C, the thread-dispersed, locality-preserving method):
+ *   * scheduling (Section IV-C: contiguous blocks per thread, with stealing):
  *     rows [r0, r1) are cut into blocks of consecutive vertices holding about
  *     `block_edges` entries each; thread t owns the t-th contiguous run of
  *     blocks and walks it in order; a thread whose run is done steals blocks

@@ -12,15 +12,19 @@
 // the mate array.
 //
 // The array holds kStaticBytes on every GPU that loads the library, until the
-// process exits.  Its device address is looked up once per device, with that
-// device current, on the first call made on it (cudaGetSymbolAddress); host
-// code never uses the array's name as an address.  Every call reuses the same
-// array: the preparation kernel clears the states, the work counter and the
-// error word at the start of each call, and two calls whose work overlaps on
-// the GPU (for example, from two host threads on two streams) race on it.
+// process exits.  Host code never uses the array's name as an address: every
+// call asks the runtime for the array's device address on the current device
+// (cudaGetSymbolAddress) and hands that to the kernels.  Asking at every call,
+// rather than once per device, keeps the address right for whatever context is
+// current, also after cudaDeviceReset or in a context that is not the device's
+// primary one (each context holds its own copy of the array); the first call in
+// a context loads the library's device code there, so make it before any
+// stream capture.  Every call reuses the same array: the preparation kernel
+// clears the states, the work counter and the error word at the start of each
+// call, and two calls whose work overlaps on the GPU (for example, from two
+// host threads on two streams) race on it.
 #include <cstdint>
 #include <cstring>
-#include <mutex>
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -40,20 +44,12 @@ static_assert(kStateWords * 4 == MM_STATIC_MAX_VERTICES, "capacity in skipper.h 
 // The fixed scratch: [control | partition table | packed byte states].
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_lock;
-unsigned char* g_dev_ptr[kMaxDevices] = {};
-
-// Device address of the scratch on the current device, looked up once.
-cudaError_t scratch_on(int dev, unsigned char** out) {
-  std::lock_guard<std::mutex> lk(g_lock);
-  if (!g_dev_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_dev_ptr[dev] = static_cast<unsigned char*>(p);
-  }
-  *out = g_dev_ptr[dev];
+// Device address of the scratch in the current context.
+cudaError_t scratch_here(unsigned char** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<unsigned char*>(p);
   return cudaSuccess;
 }
 
@@ -70,12 +66,25 @@ extern "C" mm_status mm_skipper_static(uint64_t n, uint64_t nnz, const int64_t* 
                       (unsigned long long)n, (unsigned long long)MM_STATIC_MAX_VERTICES);
     return MM_ERR_ARG;
   }
-  if (!d_offsets || (nnz && !d_nbrs) || (n && !d_mate)) return MM_ERR_ARG;
-  if (nnz && (reinterpret_cast<uintptr_t>(d_nbrs) & 15u)) return MM_ERR_ARG;
-  if (o->status_bits != 0 && o->status_bits != 8) return MM_ERR_UNSUPPORTED;
-  if (o->timing || o->use_graph || o->nosync || o->l2_persist) return MM_ERR_UNSUPPORTED;
+  auto reject = [](mm_status st, const char* why) {
+    set_error_message("mm_skipper_static: %s", why);
+    return st;
+  };
+  if (!d_offsets) return reject(MM_ERR_ARG, "null offsets");
+  if (nnz && !d_nbrs) return reject(MM_ERR_ARG, "null nbrs with nnz > 0");
+  if (n && !d_mate) return reject(MM_ERR_ARG, "null mate");
+  if (nnz && (reinterpret_cast<uintptr_t>(d_nbrs) & 15u)) return reject(MM_ERR_ARG, "nbrs must be 16-byte aligned");
+  if (reinterpret_cast<uintptr_t>(d_offsets) & 7u) return reject(MM_ERR_ARG, "offsets must be 8-byte aligned");
+  if (o->status_bits != 0 && o->status_bits != 8)
+    return reject(MM_ERR_UNSUPPORTED, "only the byte state layout (status_bits 0 or 8) fits the fixed scratch");
+  if (o->timing || o->use_graph || o->nosync || o->l2_persist)
+    return reject(MM_ERR_UNSUPPORTED, "timing, use_graph, nosync and l2_persist need a handle (mm_create_csr)");
+  if (o->stats || o->stage_windows || o->symmetric || o->id_loads == MM_ID_LOADS_SELECTIVE)
+    return reject(MM_ERR_UNSUPPORTED, "stats, stage_windows, symmetric and selective id loads need a handle "
+                                      "(mm_create_csr)");
+  if (o->id_loads > MM_ID_LOADS_SELECTIVE) return reject(MM_ERR_ARG, "id_loads must be 0, 1 or 2");
   uint64_t grain = o->grain ? o->grain : 2048;
-  if (grain % 128) return MM_ERR_ARG;
+  if (grain % 128) return reject(MM_ERR_ARG, "grain must be a multiple of 128");
   const uint64_t items = n + nnz;
   if ((items + grain - 1) / grain > kMaxUnits) {  // a coarser split fits the table
     grain = (items + kMaxUnits - 1) / kMaxUnits;
@@ -87,15 +96,22 @@ extern "C" mm_status mm_skipper_static(uint64_t n, uint64_t nnz, const int64_t* 
     return MM_ERR_ARG;
   }
   const int block = o->block_threads ? (int)o->block_threads : 512;
-  if (block < 32 || block > 512 || block % 32) return MM_ERR_ARG;
-  if (o->poison_vertex > n) return MM_ERR_ARG;
+  if (block < 32 || block > 512 || block % 32)
+    return reject(MM_ERR_ARG, "block_threads must be a multiple of 32 in [32, 512]");
+  if (o->poison_vertex > n) return reject(MM_ERR_ARG, "poison_vertex out of range");
 
+  auto cuda_fail = [](const char* what, cudaError_t e) {
+    set_error_message("mm_skipper_static: %s: %s", what, cudaGetErrorString(e));
+    return MM_ERR_CUDA;
+  };
+  cudaError_t e;
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MM_ERR_CUDA;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail("cudaGetDevice", e);
   unsigned char* base = nullptr;
-  if (scratch_on(dev, &base) != cudaSuccess) return MM_ERR_CUDA;
+  if ((e = scratch_here(&base)) != cudaSuccess) return cuda_fail("cudaGetSymbolAddress", e);
   int sms = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MM_ERR_CUDA;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return cuda_fail("cudaDeviceGetAttribute", e);
 
   SweepParams P{};
   P.n = n;
@@ -113,19 +129,20 @@ extern "C" mm_status mm_skipper_static(uint64_t n, uint64_t nnz, const int64_t* 
   P.poison = o->poison_vertex;
 
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  if (launch_prepare(P, 8, sms * 8, s, nullptr, 0) != cudaSuccess) return MM_ERR_CUDA;
-  cudaError_t e;
+  if ((e = launch_prepare(P, 8, sms * 8, s, nullptr, 0)) != cudaSuccess) return cuda_fail("prepare launch", e);
   if (o->serial) {
     e = launch_serial(P, 8, s);
   } else {
     const int per_sm = o->blocks_per_sm ? (int)o->blocks_per_sm : sweep_blocks_per_sm(8, block);
     e = launch_sweep(P, 8, sms * per_sm, block, s);
   }
-  if (e != cudaSuccess) return MM_ERR_CUDA;
+  if (e != cudaSuccess) return cuda_fail("sweep launch", e);
   uint32_t err = 0;  // the call's device status, read back into host stack memory
-  if (cudaMemcpyAsync(&err, P.err, sizeof err, cudaMemcpyDeviceToHost, s) != cudaSuccess) return MM_ERR_CUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess) return MM_ERR_CUDA;
-  if (err & kErrTimeout) return MM_ERR_TIMEOUT;
-  if (err & kErrBadId) return MM_ERR_BAD_GRAPH;
+  if ((e = cudaMemcpyAsync(&err, P.err, sizeof err, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail("status read", e);
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail("cudaStreamSynchronize", e);
+  if (err & kErrTimeout) return reject(MM_ERR_TIMEOUT, "a wait on a reserved vertex ran past spin_limit");
+  if (err & kErrBadId) return reject(MM_ERR_BAD_GRAPH, "a neighbour id >= n was met");
+  set_error_message("");
   return MM_OK;
 }

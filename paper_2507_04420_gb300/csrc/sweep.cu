@@ -2,9 +2,9 @@
 //
 // prepare_kernel: Algorithm 1 lines 3-4 (every vertex ACC, mate unmatched)
 //   fused with the merge-path partition of rows + entries into equal work
-//   units, the GPU form of the paper's blocks of consecutive vertices with
-//   about equal edge counts (Section IV-C, "thread-dispersed
-//   locality-preserving" scheduling).
+//   units, the GPU form of the paper's contiguous blocks of consecutive
+//   vertices with about equal edge counts, handed to threads with work
+//   stealing (Section IV-C).
 // sweep_kernel: Algorithm 1 lines 5-18.  Persistent warps take units from a
 //   global counter (the paper's idle threads steal work; here every unit is
 //   handed out on demand) and walk each with sweep_unit (walk.cuh): 32-row

@@ -1,20 +1,21 @@
 """Full-size parity at R-MAT scale 27 (ef 16: 134M vertices, ~4.2G CSR entries;
-2^31 listed edges for the edge-list input), in the launch configuration the
-benchmark times.
+2^31 listed edges for the edge-list input) and at the size of the benchmark's
+4096-graph batch, in the launch configurations the benchmark times.
 
-At this size the oracle cannot run whole, so the result is checked two ways:
-the device checker's verdict must be "valid maximal matching", and properties
-that define a maximal matching are checked on the host for sampled vertices
-and sampled edges (plain numpy on rows copied back, independent of the device
-checker): a named partner names the vertex back and is a neighbour; an
-unmatched sampled vertex has every neighbour matched; a sampled listed edge
-has a matched endpoint.
+Every result is checked by the oracle's exact checker on the host, over the
+whole graph (Section II-B's definition: every edge has a matched endpoint, no
+two output edges share an endpoint, every output edge exists), and the device
+checker's verdict must equal the oracle's field by field.  Beside it: the
+oracle's sequential greedy matching on the same CSR, whose size is at most
+twice any maximal matching's (both are maximal), and host-side properties on
+sampled vertices (plain numpy, independent of both checkers).
 """
 import numpy as np
 import pytest
 import torch
 
 import graphgen as gg
+import oracle
 from tests.conftest import cuda_ok
 
 pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not cuda_ok(), reason="needs a CUDA GPU")]
@@ -38,6 +39,18 @@ def rmat27():
     yield g
     del g
     torch.cuda.empty_cache()
+
+
+@pytest.fixture(scope="module")
+def rmat27_host(rmat27):
+    """The same CSR in pinned host memory (numpy views for the oracle; the
+    tensors serve the in-place path), with the oracle's SGMM pair count."""
+    h_off = rmat27.offsets.cpu().pin_memory()
+    h_nb = rmat27.nbrs.cpu().pin_memory()
+    off, nb = h_off.numpy(), h_nb.numpy()
+    _, sgmm_pairs = oracle.sgmm(off, nb)
+    yield h_off, h_nb, off, nb, len(sgmm_pairs)
+    del h_off, h_nb, off, nb
 
 
 def _sampled_rows(g, verts):
@@ -74,49 +87,61 @@ def _check_sampled_vertices(g, mate, k, seed):
     return int(matched.sum())
 
 
+def _oracle_agrees(off, nb, mate_np, device_verdict, sgmm_pairs):
+    vr = oracle.check(off, nb, mate_np)
+    assert vr.flags == 0, vr.as_dict()
+    assert device_verdict.as_dict() == vr.as_dict(), (device_verdict.as_dict(), vr.as_dict())
+    assert 2 * vr.n_pairs >= sgmm_pairs            # |M_SGMM| <= nu <= 2 |M|
+    assert 2 * vr.n_pairs == int((mate_np != NONE).sum())
+    return vr
+
+
 @pytest.mark.parametrize("symmetric", [0, 1])
-def test_csr_rmat27_in_the_benchmark_launch(skp, rmat27, symmetric):
+def test_csr_rmat27_in_the_benchmark_launch(skp, rmat27, rmat27_host, symmetric):
     g = rmat27
+    _, _, off, nb, sgmm_pairs = rmat27_host
     with skp.Graph(g.offsets, g.nbrs, check=False) as h:
         mate = h.skipper(symmetric=symmetric, **BENCH_OPTS)
         v = h.validate(mate)
-    assert v.flags == 0, v.as_dict()
     m = mate.cpu().numpy().view(np.uint32)
-    assert 2 * v.n_pairs == int((m != NONE).sum())
+    _oracle_agrees(off, nb, m, v, sgmm_pairs)
     assert _check_sampled_vertices(g, m, 200_000, seed=3 + symmetric) > 0
 
 
-def test_csr_rmat27_read_in_place_from_host_memory(skp, rmat27):
+def test_csr_rmat27_read_in_place_from_host_memory(skp, rmat27, rmat27_host):
     """The end-to-end path of the benchmark: the CSR in pinned host memory, read
     in place by the kernels (MM_HOST_MAPPED) through the host session."""
     g = rmat27
-    h_off = g.offsets.cpu().pin_memory()
-    h_nb = g.nbrs.cpu().pin_memory()
+    h_off, h_nb, off, nb, sgmm_pairs = rmat27_host
     sess = skp.HostSession(g.n, g.nnz)
     try:
         m_host = sess.run(h_off, h_nb, **BENCH_OPTS)
         assert sess.last_mode == "host_mapped"
         with skp.Graph(g.offsets, g.nbrs, check=False) as h:
             v = h.validate(m_host.cuda())
-        assert v.flags == 0, v.as_dict()
-        assert _check_sampled_vertices(g, m_host.numpy().view(np.uint32), 100_000, seed=7) > 0
+        m = m_host.numpy().view(np.uint32)
+        _oracle_agrees(off, nb, m, v, sgmm_pairs)
+        assert _check_sampled_vertices(g, m, 100_000, seed=7) > 0
     finally:
         sess.close()
-        del h_off, h_nb
 
 
-def test_edge_list_rmat27_raw_draws_in_the_benchmark_launch(skp, rmat27):
+def test_edge_list_rmat27_raw_draws_in_the_benchmark_launch(skp, rmat27, rmat27_host):
     """The 2^31 generator draws behind the CSR, as a list (repeats and loops
-    kept, no symmetrisation): the CSR is the same edge set, so it serves the
-    host-side neighbour checks."""
+    kept, no symmetrisation).  Its edge set, loops aside, is the CSR's, so the
+    oracle's CSR checker decides the verdict over the whole graph (the list
+    checker sorts the 2^31 list keys on one core, about ten minutes); for a
+    valid result the two checkers' verdicts coincide field by field, and the
+    device's list checker must give that verdict too."""
     g = rmat27
+    _, _, off, nb, sgmm_pairs = rmat27_host
     src, dst = gg.rmat_edges(SCALE, EF << SCALE, .57, .19, .19, 1, "cuda")
     try:
         with skp.EdgeList(g.n, src, dst, check=False) as h:
             mate = h.skipper(**BENCH_COO_OPTS)
             v = h.validate(mate)
-        assert v.flags == 0, v.as_dict()
         m = mate.cpu().numpy().view(np.uint32)
+        _oracle_agrees(off, nb, m, v, sgmm_pairs)
         assert _check_sampled_vertices(g, m, 200_000, seed=4) > 0
         rng = np.random.default_rng(5)
         i = torch.from_numpy(rng.integers(0, src.numel(), 2_000_000)).cuda()
@@ -126,3 +151,43 @@ def test_edge_list_rmat27_raw_draws_in_the_benchmark_launch(skp, rmat27):
     finally:
         del src, dst
         torch.cuda.empty_cache()
+
+
+@pytest.fixture(scope="module")
+def c4_batch():
+    """The benchmark's batch: 4096 graphs of 10^3..10^6 undirected edges (ER /
+    R-MAT / grid in turn), packed block-diagonally with global ids."""
+    packed, _ = gg.batch_packed(4096, 1e3, 1e6, seed=101, device="cuda", chunks=4)
+    off = packed.csr.offsets.cpu().numpy()
+    nb = packed.csr.nbrs.cpu().numpy()
+    vb = packed.vbase.cpu().numpy()
+    eb = packed.ebase.cpu().numpy()
+    _, sgmm_pairs = oracle.sgmm(off, nb)
+    yield packed, off, nb, vb, eb, len(sgmm_pairs)
+    del packed
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("bits", [8, 2])
+def test_batched_4096_graphs_in_the_benchmark_launch(skp, c4_batch, bits):
+    """One CUDA-graph replay over the whole batch: the union and every member
+    graph (rebased to local ids) are checked by the oracle; the device's
+    per-graph pair counts equal the oracle's."""
+    packed, off, nb, vb, eb, sgmm_pairs = c4_batch
+    csr = packed.csr
+    with skp.Graph(csr.offsets, csr.nbrs, check=False) as h:
+        for rep in range(2):     # the second replay reuses the captured graph
+            mate, gp = h.batched(packed.vbase, packed.ebase, graph_pairs=True, use_graph=1,
+                                 status_bits=bits, grain=8192, block_threads=512)
+            v = h.validate(mate)
+            m = mate.cpu().numpy().view(np.uint32)
+            _oracle_agrees(off, nb, m, v, sgmm_pairs)
+    gp = gp.cpu().numpy()
+    G = vb.size - 1
+    for k in range(G):
+        lo, hi, e0, e1 = int(vb[k]), int(vb[k + 1]), int(eb[k]), int(eb[k + 1])
+        loc = m[lo:hi].astype(np.int64)
+        loc = np.where(loc == NONE, NONE, loc - lo).astype(np.uint32)
+        vk = oracle.check(off[lo:hi + 1] - e0, (nb[e0:e1].astype(np.int64) - lo).astype(np.uint32), loc)
+        assert vk.flags == 0, (k, vk.as_dict())
+        assert int(gp[k]) == vk.n_pairs, k

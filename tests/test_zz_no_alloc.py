@@ -96,3 +96,31 @@ def test_static_call_rejects_graphs_beyond_its_capacity(skp):
                                    ctypes.byref(o), stream)
     assert rc == 0
     assert bool((mate[:limit] == -1).all())
+
+
+def test_static_call_refuses_what_it_cannot_run_and_says_why(skp):
+    """Options that need a handle's own memory are refused, not ignored, and
+    every refusal leaves its reason in mm_last_error()."""
+    d = gg.grid(64, 64).to("cuda")
+    mate = torch.empty(d.n, dtype=torch.int32, device="cuda")
+    for kw in (dict(stats=1), dict(stage_windows=1), dict(symmetric=1), dict(id_loads=2),
+               dict(timing=1), dict(status_bits=2)):
+        assert _static(skp, d, mate, **kw) == 6, kw            # MM_ERR_UNSUPPORTED
+        assert b"mm_skipper_static" in skp.lib.mm_last_error(), kw
+    stream = ctypes.c_void_p(int(torch.cuda.current_stream().cuda_stream))
+    o = skp.options()
+    rc = skp.lib.mm_skipper_static(d.n, d.nnz, ctypes.c_void_p(d.offsets.data_ptr()),
+                                   ctypes.c_void_p(d.nbrs.data_ptr()), None, ctypes.byref(o), stream)
+    assert rc == 1 and b"null mate" in skp.lib.mm_last_error()
+    rc = skp.lib.mm_skipper_static(d.n, d.nnz, ctypes.c_void_p(d.offsets.data_ptr()),
+                                   ctypes.c_void_p(d.nbrs.data_ptr() + 4), ctypes.c_void_p(mate.data_ptr()),
+                                   ctypes.byref(o), stream)
+    assert rc == 1 and b"16-byte aligned" in skp.lib.mm_last_error()
+    # a refused call leaves the next one working
+    assert _static(skp, d, mate) == 0, skp.lib.mm_last_error()
+    assert h_valid(skp, d, mate)
+
+
+def h_valid(skp, d, mate):
+    with skp.Graph(d.offsets, d.nbrs) as h:
+        return h.validate(mate).flags == 0
