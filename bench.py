@@ -322,11 +322,18 @@ def run_batched(args, skp):
                        "(ef 8-32) / 2-D grid in turn, packed block-diagonally with global ids",
            "graphs": G, "n": csr.n, "nnz": csr.nnz}
     mate = torch.empty(csr.n, dtype=torch.int32, device="cuda")
+    peak, peak_kind = measured_peaks()
+    sweep_bytes = 8 * (csr.n + 1) + 4 * csr.nnz
     with skp.Graph(csr.offsets, csr.nbrs) as h:
+        t0 = time.perf_counter()
         tuned = h.autotune_batched(packed.vbase, packed.ebase)
+        tune_s = time.perf_counter() - t0
         tuned.use_graph = 1
         out["tuned"] = {"grain": tuned.grain, "status_bits": tuned.status_bits,
-                        "block_threads": tuned.block_threads}
+                        "block_threads": tuned.block_threads, "warps_per_graph": tuned.warps_per_graph,
+                        "autotune_seconds": tune_s,
+                        "searched": "grain {1024,2048,4096,8192} x status_bits {2,8,32} x block {256,512} "
+                                    "x warps_per_graph {0 (no cap),1,4,16}, each checked"}
         for _ in range(3):
             h.batched(packed.vbase, packed.ebase, mate=mate, opts=tuned)
         lat = []
@@ -338,8 +345,27 @@ def run_batched(args, skp):
         v = h.validate(mate)
         if v.flags != 0:
             raise SystemExit(f"invalid batched matching: {v.as_dict()}")
+        # kernel times of the same launches outside the graph (CUDA events per kernel)
+        o_t = skp.options(status_bits=tuned.status_bits, grain=tuned.grain, block_threads=tuned.block_threads,
+                          warps_per_graph=tuned.warps_per_graph, timing=1, nosync=1)
+        for _ in range(3):
+            h.batched(packed.vbase, packed.ebase, mate=mate, opts=o_t)
+        h.sync()
+        h.timing_history()
+        for _ in range(10):
+            h.batched(packed.vbase, packed.ebase, mate=mate, opts=o_t)
+        h.sync()
+        hist = h.timing_history(256)
+        sweep_ms = statistics.mean(t["sweep_ms"] for t in hist)
+        init_ms = statistics.mean(t["init_ms"] for t in hist)
+        achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9
         out.update(p50_ms=pct(lat, 50), p99_ms=pct(lat, 99),
-                   gedges_s=csr.nnz / (pct(lat, 50) * 1e-3) / 1e9, launches_per_batch=2,
+                   gedges_s=csr.nnz / (pct(lat, 50) * 1e-3) / 1e9, launches_per_batch=3 if tuned.warps_per_graph else 2,
+                   kernel_ms={"init": init_ms, "sweep": sweep_ms},
+                   roofline={"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": None, "bytes_per_launch": sweep_bytes,
+                             "kernel": "sweep over the packed batch", "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
+                             "step_frac": sweep_bytes / (pct(lat, 50) * 1e-3) / 1e9 / peak},
                    how="mm_skipper_batched, CUDA graph replay, host wall time per batch incl. status read")
     # one mm_skipper launch sequence per graph, same data (local ids)
     parts = [gg.unpack(packed, g) for g in range(G)]
@@ -350,15 +376,49 @@ def run_batched(args, skp):
     for hg, m in zip(handles, mates):
         hg.skipper(mate=m, opts=o)
     torch.cuda.synchronize()
-    lat = []
+    lat, span = [], []
     for _ in range(max(3, args.batch_reps // 4)):
         torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
+        e0.record()
         for hg, m in zip(handles, mates):
             hg.skipper(mate=m, opts=o)
+        e1.record()
         for hg in handles:
             hg.sync()
         lat.append((time.perf_counter() - t0) * 1e3)
+        torch.cuda.synchronize()
+        span.append(e0.elapsed_time(e1))
+    # the same 4096 calls captured once into a CUDA graph and replayed: one
+    # launch per graph with no host work between the launches
+    replay = None
+    try:
+        cg = torch.cuda.CUDAGraph()
+        s_cap = torch.cuda.Stream()
+        s_cap.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s_cap):
+            with torch.cuda.graph(cg, stream=s_cap):
+                for hg, m in zip(handles, mates):
+                    hg.skipper(mate=m, opts=o)
+        torch.cuda.synchronize()
+        cg.replay()
+        torch.cuda.synchronize()
+        rt = []
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            cg.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            rt.append(e0.elapsed_time(e1))
+        replay = statistics.median(rt)
+        del cg
+    except Exception as e:   # capture refused: report the two other timings only
+        log("plain arm graph capture failed:", e)
+        torch.cuda.synchronize()
     bad = sum(handles[g].validate(mates[g]).flags != 0 for g in range(0, G, max(1, G // 64)))
     if bad:
         raise SystemExit("invalid per-graph matching")
@@ -366,101 +426,16 @@ def run_batched(args, skp):
         hg.close()
     out.update(plain_p50_ms=pct(lat, 50), plain_p99_ms=pct(lat, 99),
                plain_gedges_s=csr.nnz / (pct(lat, 50) * 1e-3) / 1e9,
-               plain_how="one mm_skipper call per graph (nosync, 2 launches each), then one status read per graph",
-               speedup_vs_plain=pct(lat, 50) / out["p50_ms"])
-    return out
-
-
-# ----------------------------------------------------------------------------
-# the other scale-27 graphs: uniform and high-skew R-MAT, every state layout
-# ----------------------------------------------------------------------------
-def time_sweep(h, mate, opts, steps, warmup):
-    """Device time per call and mean init / sweep kernel times of `steps`
-    back-to-back calls (CUDA events on the launching stream)."""
-    import torch
-    for _ in range(max(3, warmup)):
-        h.skipper(mate=mate, opts=opts)
-    h.sync()
-    h.timing_history()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        h.skipper(mate=mate, opts=opts)
-    e1.record()
-    torch.cuda.synchronize()
-    h.sync()
-    hist = h.timing_history(256)
-    return (e0.elapsed_time(e1) / steps, statistics.mean(t["sweep_ms"] for t in hist),
-            statistics.mean(t["init_ms"] for t in hist))
-
-
-def run_side_graphs(args, skp, m_headline):
-    """Config C3's companions of the headline graph: a uniform random graph with
-    the same n and edge draws, and a high-skew R-MAT (a = .7, b = c = d = .1),
-    each timed in the byte, 2-bit and 32-bit state layouts (and the 2-bit
-    layout with symmetric = 1), with the same roofline arithmetic as the
-    headline line."""
-    import graphgen as gg
-    import torch
-    scale, ef = args.scale, args.edge_factor
-    n = 1 << scale
-    chunks = (16 << max(0, scale - 27)) if scale >= 26 else 1
-    peak, peak_kind = measured_peaks()
-    gens = {
-        f"uniform{scale}": (lambda: gg.uniform(n, m_headline, seed=args.seed, device="cuda", chunks=chunks),
-                            f"{m_headline} uniform random pairs on 2^{scale} vertices (the headline R-MAT's n "
-                            "and undirected m), loops and repeats dropped, symmetrised"),
-        f"rmat{scale}_skew": (lambda: gg.rmat(scale, ef, 0.7, 0.1, 0.1, seed=args.seed, device="cuda",
-                                              chunks=chunks),
-                              f"R-MAT scale {scale}, edge factor {ef}, a/b/c/d=.7/.1/.1/.1, ids permuted, "
-                              "symmetrised, deduplicated"),
-    }
-    out = {}
-    for name, (gen, desc) in gens.items():
-        t = time.time()
-        g = gen()
-        torch.cuda.synchronize()
-        torch.cuda.empty_cache()
-        log(f"{name}: n={g.n} nnz={g.nnz} generated in {time.time() - t:.1f}s")
-        sweep_bytes = 8 * (g.n + 1) + 4 * g.nnz
-        res = {"workload": desc, "n": g.n, "nnz": g.nnz, "grain": args.grain, "block_threads": args.block,
-               "l2": "inputs larger than L2 (CSR %.1f GB); no flush" % (sweep_bytes / 1e9), "layouts": {}}
-        mate = torch.empty(g.n, dtype=torch.int32, device="cuda")
-        with skp.Graph(g.offsets, g.nbrs, check=True) as h:
-            for bits, sym in ((8, 0), (2, 0), (32, 0), (2, 1)):
-                o = skp.options(status_bits=bits, grain=args.grain, block_threads=args.block, nosync=1,
-                                timing=1, symmetric=sym)
-                ms, sweep_ms, init_ms = time_sweep(h, mate, o, args.side_steps, args.warmup)
-                v = h.validate(mate)
-                if v.flags != 0:
-                    raise SystemExit(f"invalid matching on {name} (bits {bits}): {v.as_dict()}")
-                s = {2: 0.25, 8: 1.0, 32: 4.0}[bits]
-                step_bytes = int(8 * (g.n + 1) + 4 * g.nnz + s * g.n + (4 * g.n if bits != 32 else 0))
-                achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9
-                res["layouts"][f"u{bits}" + ("_symmetric" if sym else "")] = {
-                    "ms_per_step": ms, "sweep_ms": sweep_ms, "init_ms": init_ms,
-                    "value": g.nnz / (ms * 1e-3) / 1e9, "unit": UNIT,
-                    "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                                 "frac": achieved / peak,
-                                 "traffic": None if sym else ncu_traffic(name, bits),
-                                 "bytes_per_launch": sweep_bytes,
-                                 "kernel": f"sweep_kernel<{ {2: 'TwoBit', 8: 'Byte', 32: 'Word'}[bits]}State>",
-                                 "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
-                                 "step_bytes_alg": step_bytes,
-                                 "step_frac": step_bytes / (ms * 1e-3) / 1e9 / peak},
-                    "verdict": {"flags": v.flags, "n_pairs": v.n_pairs}}
-            h.skipper(mate=mate, status_bits=8, grain=args.grain, block_threads=args.block, stats=1)
-            st = h.stats()
-            res["stats_u8"] = {k: st[k] for k in ("entries_read", "windows", "chunks", "attempts", "matches",
-                                                   "conflicts", "id_loads", "id_loads_open")}
-            res["stats_u8"]["ids_read_frac"] = st["entries_read"] / max(1, g.nnz)
-        best = max(res["layouts"].items(), key=lambda kv: kv[1]["value"])
-        res["best_layout"] = best[0]
-        out[name] = res
-        del g, mate
-        torch.cuda.empty_cache()
+               plain_device_span_ms=statistics.median(span),
+               plain_graph_replay_ms=replay,
+               plain_how="one mm_skipper call per graph (nosync; init + sweep launches and a 4-byte "
+                         "status copy each, grids sized to the graph), then one status read per graph; "
+                         "wall = host time of the loop; device span = CUDA events around the launches; "
+                         "graph replay = the same calls captured once into a CUDA graph (no host work "
+                         "between launches)",
+               speedup_vs_plain=pct(lat, 50) / out["p50_ms"],
+               speedup_vs_plain_device_span=statistics.median(span) / out["p50_ms"],
+               speedup_vs_plain_graph_replay=(replay / out["p50_ms"]) if replay else None)
     return out
 
 

@@ -359,8 +359,10 @@ def edge_list(g: CSR, order: str = "row", seed: int = 1):
     return torch.where(flip, dst, src), torch.where(flip, src, dst)
 
 
-def pack(graphs: Sequence[CSR], device=None) -> Packed:
-    """Block-diagonal packing: graph g's vertex x becomes vbase[g] + x."""
+def pack(graphs: Sequence[CSR], device=None, local: bool = False) -> Packed:
+    """Block-diagonal packing: graph g's vertex x becomes vbase[g] + x (with
+    local=True the neighbour ids stay local to each graph; only the offsets
+    become batch entry indices)."""
     if device is None:
         device = graphs[0].offsets.device if graphs else "cpu"
     ns = [g.n for g in graphs]
@@ -370,13 +372,13 @@ def pack(graphs: Sequence[CSR], device=None) -> Packed:
     if graphs:
         vbase[1:] = torch.cumsum(torch.tensor(ns, dtype=torch.int64), 0)
         ebase[1:] = torch.cumsum(torch.tensor(es, dtype=torch.int64), 0)
-    if int(vbase[-1]) >= 2**31:
+    if int(vbase[-1]) >= 2**31 and not local:
         raise ValueError("packed vertex count must stay below 2**31")
     offs = [torch.zeros(1, dtype=torch.int64, device=device)]
     nb = []
     for g, gr in enumerate(graphs):
         offs.append(gr.offsets[1:].to(device) + int(ebase[g]))
-        nb.append(gr.nbrs.to(device) + int(vbase[g]))
+        nb.append(gr.nbrs.to(device) + (0 if local else int(vbase[g])))
     offsets = torch.cat(offs)
     nbrs = torch.cat(nb) if nb else torch.zeros(0, dtype=torch.int32, device=device)
     return Packed(CSR(offsets, nbrs.to(torch.int32)), vbase.to(device), ebase.to(device))

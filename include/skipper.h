@@ -60,6 +60,8 @@ typedef enum mm_status {
 /* mm_create_csr flags */
 #define MM_CHECK_CSR 1u      /* check offsets and ids on the device (synchronous) */
 #define MM_HOST_MAPPED 2u    /* the input arrays are page-locked host memory, read in place */
+#define MM_BATCH_LOCAL_IDS 4u /* a packed batch whose member graphs keep local ids (see
+                                 mm_skipper_batched); n may exceed MM_MAX_VERTICES */
 
 typedef struct mm_graph mm_graph;
 
@@ -136,7 +138,11 @@ typedef struct mm_options {
                                 Off by default: on GB300 it is slower (the sweep
                                 is bound by instruction issue, and the staged
                                 state words are one window old).  0 = off. */
-    uint32_t reserved32;
+    uint32_t warps_per_graph; /* batched calls: at most this many work units per member
+                                graph, so at most this many warps walk one graph at a
+                                time (each graph's rows + entries are split evenly
+                                over min(warps_per_graph, ceil(items / grain))
+                                units); 0 = no cap (units of `grain` items). */
     uint64_t reserved[2];
 } mm_options;
 
@@ -236,9 +242,17 @@ mm_status mm_default_options(mm_options *o);
  * words on the current device.  With MM_CHECK_CSR the CSR is checked on the
  * device before returning (offsets[0] = 0, non-decreasing, offsets[n] = nnz,
  * every id < n) and MM_ERR_BAD_GRAPH is returned on failure.
+ * MM_BATCH_LOCAL_IDS: the CSR is a batch packed for mm_skipper_batched whose
+ * member graphs keep local ids; n (the batch's vertices) may be up to
+ * MM_MAX_BATCH_VERTICES.  Such a handle runs mm_skipper_batched,
+ * mm_autotune_batched and mm_validate_batched only (the other calls return
+ * MM_ERR_UNSUPPORTED), and MM_CHECK_CSR and MM_HOST_MAPPED are not available
+ * with it (MM_ERR_UNSUPPORTED).
  * Errors: MM_ERR_ARG (null out, n > MM_MAX_VERTICES, null arrays with n or
- * nnz > 0, misaligned d_nbrs), MM_ERR_OOM, MM_ERR_CUDA, MM_ERR_BAD_GRAPH.
+ * nnz > 0, misaligned d_nbrs), MM_ERR_OOM, MM_ERR_CUDA, MM_ERR_BAD_GRAPH,
+ * MM_ERR_UNSUPPORTED.
  */
+#define MM_MAX_BATCH_VERTICES (1ull << 40)
 mm_status mm_create_csr(uint64_t n, uint64_t nnz, const int64_t *d_offsets,
                         const uint32_t *d_nbrs, uint32_t flags, void *cuda_stream,
                         mm_graph **out);
@@ -311,21 +325,49 @@ mm_status mm_skipper(mm_graph *g, const mm_options *o, uint32_t *d_mate, uint32_
 
 /*
  * Batched Skipper over num_graphs graphs packed block-diagonally in the
- * handle's CSR with global ids: graph k owns vertices [vbase[k], vbase[k+1])
- * and entries [ebase[k], ebase[k+1]), and no entry leaves its block.  One
- * persistent sweep covers all graphs (Skipper on the union is Skipper on each
- * block, since no edge crosses blocks).  d_vbase, d_ebase: int64_t[num_graphs+1]
- * in device memory, vbase[0] = ebase[0] = 0, vbase[num_graphs] = n,
- * ebase[num_graphs] = nnz.  d_mate: uint32_t[n] (global ids).
- * d_graph_pairs: uint64_t[num_graphs] or NULL, matched pairs per graph.
- * With o->serial each graph is walked by one thread in SGMM order (so the
+ * handle's CSR: graph k owns vertices [vbase[k], vbase[k+1]) and entries
+ * [ebase[k], ebase[k+1]), and no entry leaves its block.  One persistent sweep
+ * covers all graphs (Skipper on the union is Skipper on each block, since no
+ * edge crosses blocks).  d_vbase, d_ebase: int64_t[num_graphs+1] in device
+ * memory, vbase[0] = ebase[0] = 0, vbase[num_graphs] = n, ebase[num_graphs] =
+ * nnz, non-decreasing.  d_mate: uint32_t[n].  d_graph_pairs: uint64_t[num_graphs]
+ * or NULL, matched pairs per graph.
+ *
+ * Ids.  On a handle made without MM_BATCH_LOCAL_IDS the neighbour ids and the
+ * mate entries are global (vertex x of graph k is vbase[k] + x).  On a handle
+ * made with MM_BATCH_LOCAL_IDS they are local: graph k's entries hold ids in
+ * [0, vbase[k+1] - vbase[k]), and d_mate[vbase[k] + x] receives the local id of
+ * x's partner; the offsets stay global entry indices.  The batch's total n may
+ * then exceed MM_MAX_VERTICES (each graph's n may not).
+ *
+ * Work split.  Without a cap (warps_per_graph = 0) on a global-id handle, the
+ * union is split into merge-path units of `grain` rows + entries (units may
+ * span graphs).  With local ids or warps_per_graph > 0, every graph is split
+ * on its own into min(warps_per_graph, ceil(items / grain)) units (no cap when
+ * 0); those tables are computed on the device from d_vbase / d_ebase at every
+ * call.  With o->serial each graph is walked by one thread in SGMM order (the
  * result equals sequential greedy MM on every graph).  With o->use_graph the
- * launches run as a CUDA graph captured once per handle and options, whose
- * kernel arguments are updated per call.
+ * launches run as a CUDA graph built once per handle and option set, whose
+ * kernel arguments are updated per call (new buffers or contents need no new
+ * graph).  stats and poison_vertex are not available with local ids or a cap
+ * (MM_ERR_UNSUPPORTED).
  */
 mm_status mm_skipper_batched(mm_graph *g, uint64_t num_graphs, const int64_t *d_vbase,
                              const int64_t *d_ebase, const mm_options *o, uint32_t *d_mate,
                              uint64_t *d_graph_pairs, void *cuda_stream);
+
+/*
+ * The exact checker (Section II-B) over a batch laid out as for
+ * mm_skipper_batched, global or local ids as the handle says: every member
+ * graph is checked on its own vertices and entries and the counts are summed
+ * into one verdict.  first_bad_vertex is a batch vertex index (vbase[k] + x),
+ * first_uncovered a batch entry index.  On a global-id handle the verdict
+ * equals mm_validate's.  Synchronous.  Errors: MM_ERR_ARG, MM_ERR_CUDA,
+ * MM_ERR_OOM.
+ */
+mm_status mm_validate_batched(mm_graph *g, uint64_t num_graphs, const int64_t *d_vbase,
+                              const int64_t *d_ebase, const uint32_t *d_mate, mm_verdict *h_out,
+                              void *cuda_stream);
 
 /*
  * Exact checker on the device (Section II-B; counting rules above).
@@ -363,10 +405,12 @@ mm_status mm_get_timing(mm_graph *g, mm_timing *out);
 mm_status mm_timing_history(mm_graph *g, mm_timing *out, uint32_t max, uint32_t *count);
 
 /*
- * Autotuner for mm_skipper_batched: times the candidate (grain, status_bits
- * in {2, 8, 32}, block_threads) settings on this batch with CUDA events, keeps the fastest
- * whose result passes the device checker, and writes it into *o (other fields
- * of *o are kept).  d_mate_scratch: uint32_t[n].  Synchronous.
+ * Autotuner for mm_skipper_batched: times the candidate settings -- grain in
+ * {1024, 2048, 4096, 8192}, status_bits in {2, 8, 32}, block_threads in {256,
+ * 512}, warps_per_graph in {0 (no cap), 1, 4, 16} -- on this batch with CUDA
+ * events, keeps the fastest whose result passes the device checker
+ * (mm_validate_batched), and writes it into *o (other fields of *o are kept).
+ * d_mate_scratch: uint32_t[n].  Synchronous.
  */
 mm_status mm_autotune_batched(mm_graph *g, uint64_t num_graphs, const int64_t *d_vbase,
                               const int64_t *d_ebase, uint32_t *d_mate_scratch,

@@ -78,7 +78,7 @@ def _need(t: torch.Tensor, name: str, dtypes):
 
 _U32 = tuple(d for d in (torch.int32, getattr(torch, "uint32", None)) if d is not None)
 
-MM_CHECK_CSR, MM_HOST_MAPPED = 1, 2
+MM_CHECK_CSR, MM_HOST_MAPPED, MM_BATCH_LOCAL_IDS = 1, 2, 4
 
 
 def _need_pinned(t: torch.Tensor, name: str, dtypes):
@@ -101,7 +101,7 @@ class Graph:
     over the host link only the entries it reads."""
 
     def __init__(self, offsets: torch.Tensor, nbrs: torch.Tensor, check: bool = True, stream=None,
-                 host_mapped: bool = False):
+                 host_mapped: bool = False, local_ids: bool = False):
         if host_mapped:
             _need_pinned(offsets, "offsets", (torch.int64,))
             if nbrs.numel():   # an empty array is never read
@@ -114,7 +114,8 @@ class Graph:
         self.offsets, self.nbrs = offsets, nbrs
         self.n = offsets.numel() - 1
         self.nnz = nbrs.numel()
-        flags = (MM_CHECK_CSR if check else 0) | (MM_HOST_MAPPED if host_mapped else 0)
+        flags = ((MM_CHECK_CSR if check else 0) | (MM_HOST_MAPPED if host_mapped else 0) |
+                 (MM_BATCH_LOCAL_IDS if local_ids else 0))
         h = ctypes.c_void_p()
         _check(lib.mm_create_csr(self.n, self.nnz, _ptr(offsets), _ptr(nbrs) if self.nnz else None,
                                  flags, _stream_ptr(stream), ctypes.byref(h)),
@@ -159,6 +160,17 @@ class Graph:
                                       _ptr(mate), _ptr(gp), _stream_ptr(stream)),
                "mm_skipper_batched")
         return (mate, gp) if graph_pairs else mate
+
+    def validate_batched(self, vbase: torch.Tensor, ebase: torch.Tensor, mate: torch.Tensor,
+                         stream=None) -> Verdict:
+        """One verdict over every member graph of a packed batch (mm_validate_batched)."""
+        _need(vbase, "vbase", (torch.int64,))
+        _need(ebase, "ebase", (torch.int64,))
+        _need(mate, "mate", _U32)
+        v = Verdict()
+        _check(lib.mm_validate_batched(self._h, vbase.numel() - 1, _ptr(vbase), _ptr(ebase), _ptr(mate),
+                                       ctypes.byref(v), _stream_ptr(stream)), "mm_validate_batched")
+        return v
 
     def autotune_batched(self, vbase: torch.Tensor, ebase: torch.Tensor, stream=None,
                          opts: Optional[Options] = None, **kw) -> Options:

@@ -19,7 +19,7 @@ CSRC = os.path.join(_PKG, "csrc")
 INCLUDE = os.path.join(_ROOT, "include")
 LIB_DIR = os.path.join(_PKG, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libskipper.so")
-SOURCES = ["sweep.cu", "check.cu", "api.cu", "noalloc.cu", "multi.cu", "coo.cu", "server.cu"]
+SOURCES = ["sweep.cu", "check.cu", "api.cu", "noalloc.cu", "multi.cu", "coo.cu", "server.cu", "batch.cu"]
 HEADERS = ["state.cuh", "internal.h", "walk.cuh", "checkwalk.cuh"]
 
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -89,7 +89,7 @@ class Options(ctypes.Structure):
         ("symmetric", ctypes.c_uint32),
         ("id_loads", ctypes.c_uint32),
         ("stage_windows", ctypes.c_uint32),
-        ("reserved32", ctypes.c_uint32),
+        ("warps_per_graph", ctypes.c_uint32),
         ("reserved", ctypes.c_uint64 * 2),
     ]
 
@@ -197,6 +197,7 @@ SYMBOLS = [
     ("mm_skipper", _I, [_P, ctypes.POINTER(Options), _P, _P, _U64, _P, _P]),
     ("mm_skipper_batched", _I, [_P, _U64, _P, _P, ctypes.POINTER(Options), _P, _P, _P]),
     ("mm_validate", _I, [_P, _P, _P, _U64, ctypes.POINTER(Verdict), _P]),
+    ("mm_validate_batched", _I, [_P, _U64, _P, _P, _P, ctypes.POINTER(Verdict), _P]),
     ("mm_sync", _I, [_P, _P]),
     ("mm_get_stats", _I, [_P, ctypes.POINTER(Stats), _P]),
     ("mm_get_timing", _I, [_P, ctypes.POINTER(Timing)]),

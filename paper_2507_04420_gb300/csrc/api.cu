@@ -44,9 +44,10 @@ struct BatchGraph {
   bool valid = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaGraphNode_t n_prepare = nullptr, n_sweep = nullptr, n_pairs = nullptr, n_copy = nullptr;
+  cudaGraphNode_t n_plan = nullptr, n_prepare = nullptr, n_sweep = nullptr, n_pairs = nullptr,
+                  n_copy = nullptr;
   // signature of the options the graph was built for
-  uint32_t status_bits = 0, serial = 0, grain = 0, block = 0, blocks_per_sm = 0;
+  uint32_t status_bits = 0, serial = 0, grain = 0, block = 0, blocks_per_sm = 0, wpg = 0;
   bool sym = false;
   bool with_pairs = false;
   uint64_t num_graphs = 0;
@@ -97,6 +98,15 @@ struct mm_graph {
   bool hist_ready = false;
   mm_timing timing{};
   BatchGraph bg;
+  // batches partitioned per member graph (batch.cu): local ids, warps-per-graph cap
+  bool local_ids = false;             // made with MM_BATCH_LOCAL_IDS
+  uint64_t state_words = 0;           // words allocated at `state`
+  uint64_t* btab = nullptr;           // ubase [G+1] | sbase [G+1] | totals [2]
+  uint64_t btab_graphs = 0;
+  uint32_t* bgid = nullptr;
+  int64_t* bpart = nullptr;
+  uint64_t bunits_cap = 0;
+  BatchGraph bg2;                     // the CUDA graph of these launches
 };
 
 namespace {
@@ -114,6 +124,7 @@ struct Resolved {
   int block;
   int blocks_per_sm;
   bool nosync, timing, use_graph, l2_persist, stats, sym, sel, stage;
+  uint32_t wpg;
   uint64_t spin_limit, poison;
 };
 
@@ -143,10 +154,11 @@ mm_status resolve(const mm_graph* g, const mm_options* o, Resolved* r) {
   if (o->id_loads > MM_ID_LOADS_SELECTIVE) return fail(MM_ERR_ARG, "id_loads must be 0, 1 or 2 (got %u)", o->id_loads);
   r->sel = o->id_loads == MM_ID_LOADS_SELECTIVE || (o->id_loads == MM_ID_LOADS_AUTO && g->host_mapped);
   r->stage = o->stage_windows != 0;
+  r->wpg = o->warps_per_graph;
   r->spin_limit = o->spin_limit ? o->spin_limit : kDefaultSpin;
   r->poison = o->poison_vertex;
   if (r->poison > g->n) return fail(MM_ERR_ARG, "poison_vertex out of range");
-  if (r->word && g->n > MM_MAX_VERTICES) return fail(MM_ERR_ARG, "n too large for 32-bit states");
+  if (r->word && g->n > MM_MAX_VERTICES && !g->local_ids) return fail(MM_ERR_ARG, "n too large for 32-bit states");
   return MM_OK;
 }
 
@@ -166,6 +178,22 @@ int sweep_grid(const mm_graph* g, const Resolved& r) {
 }
 
 int prepare_grid(const mm_graph* g) { return g->num_sms * 8; }
+
+// Grids of one mm_skipper call sized to its graph: a small graph gets only the
+// blocks it can use (its units for the sweep, its fills and units for the
+// preparation), so a call on a 1k-edge graph does not launch a full
+// persistent grid.
+int prepare_grid_for(const mm_graph* g, uint64_t units) {
+  const uint64_t items = (g->n / 4 + 1 > units + 1 ? g->n / 4 + 1 : units + 1);
+  const uint64_t blocks = (items + 255) / 256;
+  return blocks < (uint64_t)prepare_grid(g) ? (int)blocks : prepare_grid(g);
+}
+int sweep_grid_for(const mm_graph* g, const Resolved& r, uint64_t units) {
+  const uint64_t warps = (uint64_t)(r.block / 32);
+  const uint64_t blocks = (units + warps - 1) / warps;
+  const int full = sweep_grid(g, r);
+  return blocks < (uint64_t)full ? (int)(blocks ? blocks : 1) : full;
+}
 
 SweepParams make_params(mm_graph* g, const Resolved& r, uint32_t* d_mate) {
   SweepParams P{};
@@ -306,7 +334,7 @@ mm_status map_host(const T** p, const char* what) {
 }
 
 mm_status check_flags_and_device(uint32_t flags) {
-  if (flags & ~(MM_CHECK_CSR | MM_HOST_MAPPED)) return fail(MM_ERR_ARG, "unknown flags 0x%x", flags);
+  if (flags & ~(MM_CHECK_CSR | MM_HOST_MAPPED | MM_BATCH_LOCAL_IDS)) return fail(MM_ERR_ARG, "unknown flags 0x%x", flags);
   int ndev = 0;
   CUDA_TRY(cudaGetDeviceCount(&ndev));
   if (ndev <= 0) return fail(MM_ERR_CUDA, "no CUDA device");
@@ -334,6 +362,7 @@ mm_status new_handle(uint64_t n, uint64_t items, cudaStream_t s, mm_graph** out)
   g->nnz = items;
   const uint64_t words = (n + 3) / 4 + 4;
   if ((st = step(cudaMalloc(&g->state, words * sizeof(uint32_t)), "state")) != MM_OK) return st;
+  g->state_words = words;
   if ((st = step(cudaMalloc(&g->ctrl, 32 * sizeof(unsigned long long)), "control words")) != MM_OK) return st;
   if ((st = step(cudaMemsetAsync(g->ctrl, 0, 32 * sizeof(unsigned long long), s), "control words")) != MM_OK)
     return st;
@@ -501,7 +530,11 @@ mm_status mm_create_csr(uint64_t n, uint64_t nnz, const int64_t* d_offsets, cons
   g_err[0] = 0;
   if (!out) return fail(MM_ERR_ARG, "null out");
   *out = nullptr;
-  if (n > MM_MAX_VERTICES) return fail(MM_ERR_ARG, "n = %llu exceeds %llu", (unsigned long long)n, MM_MAX_VERTICES);
+  const bool local = (flags & MM_BATCH_LOCAL_IDS) != 0;
+  if (local && (flags & (MM_CHECK_CSR | MM_HOST_MAPPED)))
+    return fail(MM_ERR_UNSUPPORTED, "MM_BATCH_LOCAL_IDS takes neither MM_CHECK_CSR nor MM_HOST_MAPPED");
+  const uint64_t max_n = local ? MM_MAX_BATCH_VERTICES : MM_MAX_VERTICES;
+  if (n > max_n) return fail(MM_ERR_ARG, "n = %llu exceeds %llu", (unsigned long long)n, (unsigned long long)max_n);
   if (!d_offsets) return fail(MM_ERR_ARG, "null offsets");
   if (nnz && !d_nbrs) return fail(MM_ERR_ARG, "null nbrs with nnz > 0");
   auto aligned = [&]() {
@@ -525,6 +558,7 @@ mm_status mm_create_csr(uint64_t n, uint64_t nnz, const int64_t* d_offsets, cons
   g->offsets = d_offsets;
   g->nbrs = d_nbrs;
   g->host_mapped = (flags & MM_HOST_MAPPED) != 0;
+  g->local_ids = local;
   if ((ms = ensure_part(g, (n + nnz + kDefaultGrain - 1) / kDefaultGrain)) != MM_OK) {
     mm_destroy(g);
     return ms;
@@ -544,6 +578,7 @@ mm_status mm_skipper(mm_graph* g, const mm_options* o, uint32_t* d_mate, uint32_
   g_err[0] = 0;
   mm_status st = check_handle(g);
   if (st != MM_OK) return st;
+  if (g->local_ids) return fail(MM_ERR_UNSUPPORTED, "a MM_BATCH_LOCAL_IDS handle runs batched calls only");
   if (!d_mate && g->n) return fail(MM_ERR_ARG, "null mate");
   if (d_pairs && !cap) return fail(MM_ERR_ARG, "pairs given with cap = 0");
   Resolved r;
@@ -569,12 +604,12 @@ mm_status mm_skipper(mm_graph* g, const mm_options* o, uint32_t* d_mate, uint32_
     ev = next_hist(g, units, d_pairs || d_count);
     CUDA_TRY(cudaEventRecord(ev[0], s));
   }
-  CUDA_TRY(launch_prepare(P, r.bits, prepare_grid(g), s, nullptr, 0));
+  CUDA_TRY(launch_prepare(P, r.bits, prepare_grid_for(g, units), s, nullptr, 0));
   if (ev) CUDA_TRY(cudaEventRecord(ev[1], s));
   L2Window win;
   if (!r.serial) {
     if ((st = win.open(g, r, s, P.state, r.word ? g->n * 4 : packed_words(g->n, r.bits) * 4)) != MM_OK) return st;
-    CUDA_TRY(launch_sweep(P, r.bits, sweep_grid(g, r), r.block, s));
+    CUDA_TRY(launch_sweep(P, r.bits, sweep_grid_for(g, r, units), r.block, s));
     if ((st = win.close()) != MM_OK) return st;
   } else {
     CUDA_TRY(launch_serial(P, r.bits, s));
@@ -745,6 +780,212 @@ mm_status update_batch_graph(mm_graph* g, const Resolved& r, uint64_t num_graphs
   return MM_OK;
 }
 
+// ---- batches partitioned per member graph (batch.cu) ----
+
+// Device tables for num_graphs graphs split into units of at least `grain`
+// items: ubase / sbase / totals, unit -> graph, unit starts; and room for the
+// states of every graph at a word boundary of its own.
+mm_status ensure_batch_scratch(mm_graph* g, uint64_t num_graphs, uint64_t grain, int bits) {
+  if (!g->btab || g->btab_graphs < num_graphs) {
+    if (g->btab) cudaFree(g->btab);
+    g->btab = nullptr;
+    g->btab_graphs = 0;
+    CUDA_TRY(cudaMalloc(&g->btab, (2 * (num_graphs + 1) + 2) * sizeof(uint64_t)));
+    g->btab_graphs = num_graphs;
+  }
+  // sum over graphs of ceil(items_g / grain) <= (n + nnz) / grain + num_graphs
+  const uint64_t units = (g->n + g->nnz) / grain + num_graphs + 1;
+  if (!g->bgid || g->bunits_cap < units) {
+    if (g->bgid) cudaFree(g->bgid);
+    if (g->bpart) cudaFree(g->bpart);
+    g->bgid = nullptr;
+    g->bpart = nullptr;
+    g->bunits_cap = 0;
+    CUDA_TRY(cudaMalloc(&g->bgid, (units + 1) * sizeof(uint32_t)));
+    CUDA_TRY(cudaMalloc(&g->bpart, 2 * (units + 1) * sizeof(int64_t)));
+    g->bunits_cap = units;
+  }
+  if (bits != 32) {
+    const uint64_t words = packed_words(g->n, bits) + (g->local_ids ? num_graphs : 0) + 4;
+    if (g->state_words < words) {
+      cudaFree(g->state);
+      g->state = nullptr;
+      g->state_words = 0;
+      CUDA_TRY(cudaMalloc(&g->state, words * sizeof(uint32_t)));
+      g->state_words = words;
+    }
+  }
+  return MM_OK;
+}
+
+BatchParams batch_params(mm_graph* g, const Resolved& r, uint64_t num_graphs, const int64_t* d_vbase,
+                         const int64_t* d_ebase, uint32_t* d_mate, uint64_t* d_graph_pairs) {
+  BatchParams B{};
+  B.P.n = g->n;
+  B.P.nnz = g->nnz;
+  B.P.offsets = g->offsets;
+  B.P.nbrs = g->nbrs;
+  B.P.mate = d_mate;
+  B.P.state = r.word ? d_mate : g->state;
+  B.P.work = work_ptr(g);
+  B.P.err = err_ptr(g);
+  B.P.spin_limit = r.spin_limit;
+  B.vbase = d_vbase;
+  B.ebase = d_ebase;
+  B.num_graphs = num_graphs;
+  B.ubase = g->btab;
+  B.sbase = g->btab + num_graphs + 1;
+  B.totals = g->btab + 2 * (num_graphs + 1);
+  B.gid = g->bgid;
+  B.part = g->bpart;
+  B.grain = r.grain;
+  B.wpg = r.wpg;
+  B.local = g->local_ids ? 1u : 0u;
+  B.graph_pairs = d_graph_pairs;
+  return B;
+}
+
+struct BatchLaunch {
+  BatchKernels k;
+  dim3 plan_grid, plan_block, prep_grid, prep_block, sweep_grid, sweep_block, pairs_grid, pairs_block;
+};
+
+BatchLaunch batch_launch(const mm_graph* g, const Resolved& r, uint64_t num_graphs) {
+  BatchLaunch L{};
+  get_batch_kernels(r.bits, g->local_ids, r.serial, r.sym && !r.serial, &L.k);
+  L.plan_grid = dim3(1);
+  L.plan_block = dim3(batch_plan_threads());
+  L.prep_grid = dim3(prepare_grid(g));
+  L.prep_block = dim3(256);
+  if (r.serial) {
+    L.sweep_grid = dim3((unsigned)((num_graphs + 127) / 128));
+    L.sweep_block = dim3(128);
+  } else {
+    const int per_sm = r.blocks_per_sm > 0 ? r.blocks_per_sm
+                                           : batch_sweep_blocks_per_sm(r.bits, g->local_ids, r.sym, r.block);
+    L.sweep_grid = dim3(g->num_sms * per_sm);
+    L.sweep_block = dim3(r.block);
+  }
+  L.pairs_grid = dim3(prepare_grid(g));
+  L.pairs_block = dim3(256);
+  return L;
+}
+
+// A CUDA graph of the launches: plan -> prepare -> sweep -> (pairs) -> status copy.
+mm_status build_batch_graph2(mm_graph* g, const Resolved& r, uint64_t num_graphs, BatchParams B) {
+  BatchGraph& b = g->bg2;
+  if (b.exec) cudaGraphExecDestroy(b.exec);
+  if (b.graph) cudaGraphDestroy(b.graph);
+  b = BatchGraph{};
+  const BatchLaunch L = batch_launch(g, r, num_graphs);
+  CUDA_TRY(cudaGraphCreate(&b.graph, 0));
+  int states = 1;
+  void* a1[] = {&B};
+  void* a2[] = {&B, &states};
+  cudaKernelNodeParams kp{};
+  kp.func = const_cast<void*>(L.k.plan);
+  kp.gridDim = L.plan_grid;
+  kp.blockDim = L.plan_block;
+  kp.kernelParams = a1;
+  CUDA_TRY(cudaGraphAddKernelNode(&b.n_plan, b.graph, nullptr, 0, &kp));
+  kp.func = const_cast<void*>(L.k.prepare);
+  kp.gridDim = L.prep_grid;
+  kp.blockDim = L.prep_block;
+  kp.kernelParams = a2;
+  CUDA_TRY(cudaGraphAddKernelNode(&b.n_prepare, b.graph, &b.n_plan, 1, &kp));
+  kp.func = const_cast<void*>(L.k.sweep);
+  kp.gridDim = L.sweep_grid;
+  kp.blockDim = L.sweep_block;
+  kp.kernelParams = a1;
+  CUDA_TRY(cudaGraphAddKernelNode(&b.n_sweep, b.graph, &b.n_prepare, 1, &kp));
+  cudaGraphNode_t last = b.n_sweep;
+  if (B.graph_pairs) {
+    kp.func = const_cast<void*>(L.k.pairs);
+    kp.gridDim = L.pairs_grid;
+    kp.blockDim = L.pairs_block;
+    kp.kernelParams = a1;
+    CUDA_TRY(cudaGraphAddKernelNode(&b.n_pairs, b.graph, &last, 1, &kp));
+    last = b.n_pairs;
+  }
+  CUDA_TRY(cudaGraphAddMemcpyNode1D(&b.n_copy, b.graph, &last, 1, g->h_err, err_ptr(g), sizeof(uint32_t),
+                                    cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaGraphInstantiate(&b.exec, b.graph, 0));
+  b.valid = true;
+  b.status_bits = (uint32_t)r.bits;
+  b.serial = r.serial;
+  b.sym = r.sym;
+  b.grain = r.grain;
+  b.wpg = r.wpg;
+  b.block = (uint32_t)r.block;
+  b.blocks_per_sm = (uint32_t)r.blocks_per_sm;
+  b.with_pairs = B.graph_pairs != nullptr;
+  b.num_graphs = num_graphs;
+  return MM_OK;
+}
+
+// New arguments (buffers, tables) for the kernel nodes of the built graph.
+mm_status update_batch_graph2(mm_graph* g, BatchParams B) {
+  BatchGraph& b = g->bg2;
+  int states = 1;
+  void* a1[] = {&B};
+  void* a2[] = {&B, &states};
+  cudaGraphNode_t nodes[] = {b.n_plan, b.n_prepare, b.n_sweep, b.n_pairs};
+  for (int i = 0; i < 4; ++i) {
+    if (!nodes[i]) continue;
+    cudaKernelNodeParams kp{};
+    CUDA_TRY(cudaGraphKernelNodeGetParams(nodes[i], &kp));
+    kp.kernelParams = i == 1 ? a2 : a1;
+    kp.extra = nullptr;
+    CUDA_TRY(cudaGraphExecKernelNodeSetParams(b.exec, nodes[i], &kp));
+  }
+  return MM_OK;
+}
+
+mm_status run_batched2(mm_graph* g, const Resolved& r, uint64_t num_graphs, const int64_t* d_vbase,
+                       const int64_t* d_ebase, uint32_t* d_mate, uint64_t* d_graph_pairs, cudaStream_t s) {
+  if (r.stats || r.poison)
+    return fail(MM_ERR_UNSUPPORTED, "stats and poison_vertex are not available with local ids or warps_per_graph");
+  if (num_graphs >= (1ull << 32)) return fail(MM_ERR_ARG, "num_graphs must stay below 2^32");
+  mm_status st;
+  if ((st = ensure_batch_scratch(g, num_graphs, r.grain, r.bits)) != MM_OK) return st;
+  BatchParams B = batch_params(g, r, num_graphs, d_vbase, d_ebase, d_mate, d_graph_pairs);
+  if (r.use_graph) {
+    BatchGraph& b = g->bg2;
+    const bool same = b.valid && b.status_bits == (uint32_t)r.bits && b.serial == (uint32_t)r.serial &&
+                      b.sym == r.sym && b.grain == r.grain && b.wpg == r.wpg && b.block == (uint32_t)r.block &&
+                      b.blocks_per_sm == (uint32_t)r.blocks_per_sm && b.with_pairs == (d_graph_pairs != nullptr) &&
+                      b.num_graphs == num_graphs;
+    if (!same) {
+      if ((st = build_batch_graph2(g, r, num_graphs, B)) != MM_OK) return st;
+    } else {
+      if ((st = update_batch_graph2(g, B)) != MM_OK) return st;
+    }
+    CUDA_TRY(cudaGraphLaunch(b.exec, s));
+    if (r.nosync) return MM_OK;
+    return read_err(g, s);
+  }
+  const BatchLaunch L = batch_launch(g, r, num_graphs);
+  cudaEvent_t* ev = nullptr;
+  if (r.timing) {
+    if ((st = ensure_hist(g)) != MM_OK) return st;
+    ev = next_hist(g, 0, d_graph_pairs != nullptr);
+    CUDA_TRY(cudaEventRecord(ev[0], s));
+  }
+  int states = 1;
+  void* a1[] = {&B};
+  void* a2[] = {&B, &states};
+  CUDA_TRY(cudaLaunchKernel(L.k.plan, L.plan_grid, L.plan_block, a1, 0, s));
+  CUDA_TRY(cudaLaunchKernel(L.k.prepare, L.prep_grid, L.prep_block, a2, 0, s));
+  if (ev) CUDA_TRY(cudaEventRecord(ev[1], s));
+  CUDA_TRY(cudaLaunchKernel(L.k.sweep, L.sweep_grid, L.sweep_block, a1, 0, s));
+  if (ev) CUDA_TRY(cudaEventRecord(ev[2], s));
+  if (d_graph_pairs) CUDA_TRY(cudaLaunchKernel(L.k.pairs, L.pairs_grid, L.pairs_block, a1, 0, s));
+  if (ev) CUDA_TRY(cudaEventRecord(ev[3], s));
+  CUDA_TRY(cudaMemcpyAsync(g->h_err, err_ptr(g), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  if (r.nosync) return MM_OK;
+  return read_err(g, s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -763,6 +1004,8 @@ mm_status mm_skipper_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d_
   if ((st = resolve(g, o, &r)) != MM_OK) return st;
   if (r.timing && r.use_graph) return fail(MM_ERR_UNSUPPORTED, "timing with use_graph");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (g->local_ids || r.wpg)
+    return run_batched2(g, r, num_graphs, d_vbase, d_ebase, d_mate, d_graph_pairs, s);
   const uint64_t units = (g->n + g->nnz + r.grain - 1) / r.grain;
   if ((st = ensure_part(g, units)) != MM_OK) return st;
   SweepParams P = make_params(g, r, d_mate);
@@ -816,6 +1059,7 @@ mm_status mm_validate(mm_graph* g, const uint32_t* d_mate, const uint32_t* d_pai
   g_err[0] = 0;
   mm_status st = check_handle(g);
   if (st != MM_OK) return st;
+  if (g->local_ids) return fail(MM_ERR_UNSUPPORTED, "a MM_BATCH_LOCAL_IDS handle is checked by mm_validate_batched");
   if (!h_out) return fail(MM_ERR_ARG, "null verdict");
   if (!d_mate && g->n) return fail(MM_ERR_ARG, "null mate");
   if (d_pairs && count && !g->seen_bits)
@@ -856,6 +1100,47 @@ mm_status mm_validate(mm_graph* g, const uint32_t* d_mate, const uint32_t* d_pai
   return MM_OK;
 }
 
+mm_status mm_validate_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d_vbase,
+                              const int64_t* d_ebase, const uint32_t* d_mate, mm_verdict* h_out,
+                              void* cuda_stream) {
+  g_err[0] = 0;
+  mm_status st = check_handle(g);
+  if (st != MM_OK) return st;
+  if (g->coo) return fail(MM_ERR_UNSUPPORTED, "batched calls take a CSR handle");
+  if (!h_out) return fail(MM_ERR_ARG, "null verdict");
+  if (num_graphs == 0 || num_graphs >= (1ull << 32)) return fail(MM_ERR_ARG, "num_graphs must be in [1, 2^32)");
+  if (!d_vbase || !d_ebase) return fail(MM_ERR_ARG, "null vbase / ebase");
+  if (!d_mate && g->n) return fail(MM_ERR_ARG, "null mate");
+  if ((st = ensure_batch_scratch(g, num_graphs, kCheckGrain, 32)) != MM_OK) return st;
+  Resolved r{};
+  r.grain = (uint32_t)kCheckGrain;
+  r.bits = 32;
+  r.word = true;
+  const BatchParams B = batch_params(g, r, num_graphs, d_vbase, d_ebase, const_cast<uint32_t*>(d_mate), nullptr);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  CUDA_TRY(launch_validate_batch(B, counters_ptr(g), prepare_grid(g), s));
+  CUDA_TRY(cudaMemcpyAsync(g->h_counters, counters_ptr(g), 9 * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  const unsigned long long* c = g->h_counters;
+  mm_verdict v{};
+  v.n_matched = c[0];
+  v.n_pairs = c[1];
+  v.n_bad_range = c[2];
+  v.n_asym = c[3];
+  v.n_nonedge = c[4];
+  v.n_uncovered = c[5];
+  v.n_pairs_bad = c[6];
+  v.first_bad_vertex = c[7];
+  v.first_uncovered = c[8];
+  if (v.n_bad_range) v.flags |= MM_V_RANGE;
+  if (v.n_asym) v.flags |= MM_V_ASYM;
+  if (v.n_nonedge) v.flags |= MM_V_NONEDGE;
+  if (v.n_uncovered) v.flags |= MM_V_UNCOVERED;
+  *h_out = v;
+  return MM_OK;
+}
+
 mm_status mm_autotune_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d_vbase,
                               const int64_t* d_ebase, uint32_t* d_mate_scratch, mm_options* o,
                               void* cuda_stream) {
@@ -867,16 +1152,19 @@ mm_status mm_autotune_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d
   static const uint32_t grains[] = {1024, 2048, 4096, 8192};
   static const uint32_t bits[] = {2, 8, 32};
   static const uint32_t blocks[] = {256, 512};
+  static const uint32_t wpgs[] = {0, 1, 4, 16};
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   float best = 1e30f;
   mm_options best_o = *o;
   for (uint32_t gr : grains)
     for (uint32_t sb : bits)
-      for (uint32_t bt : blocks) {
+      for (uint32_t bt : blocks)
+        for (uint32_t wg : wpgs) {
         mm_options c = *o;
         c.grain = gr;
         c.status_bits = sb;
         c.block_threads = bt;
+        c.warps_per_graph = wg;
         c.serial = 0;
         c.use_graph = 0;
         c.nosync = 0;
@@ -890,7 +1178,7 @@ mm_status mm_autotune_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d
           if (rep > 0) total += t.total_ms;
         }
         mm_verdict v;
-        if ((st = mm_validate(g, d_mate_scratch, nullptr, 0, &v, s)) != MM_OK) return st;
+        if ((st = mm_validate_batched(g, num_graphs, d_vbase, d_ebase, d_mate_scratch, &v, s)) != MM_OK) return st;
         if (v.flags) return fail(MM_ERR_CUDA, "autotune candidate gave an invalid matching (flags 0x%x)", v.flags);
         if (total < best) {
           best = total;
@@ -898,8 +1186,9 @@ mm_status mm_autotune_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d
           best_o.grain = gr;
           best_o.status_bits = sb;
           best_o.block_threads = bt;
+          best_o.warps_per_graph = wg;
         }
-      }
+        }
   *o = best_o;
   return MM_OK;
 }
@@ -908,6 +1197,11 @@ mm_status mm_destroy(mm_graph* g) {
   if (!g) return MM_OK;
   if (g->bg.exec) cudaGraphExecDestroy(g->bg.exec);
   if (g->bg.graph) cudaGraphDestroy(g->bg.graph);
+  if (g->bg2.exec) cudaGraphExecDestroy(g->bg2.exec);
+  if (g->bg2.graph) cudaGraphDestroy(g->bg2.graph);
+  if (g->btab) cudaFree(g->btab);
+  if (g->bgid) cudaFree(g->bgid);
+  if (g->bpart) cudaFree(g->bpart);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
   for (auto& set : g->hist)

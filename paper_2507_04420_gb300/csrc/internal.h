@@ -19,6 +19,36 @@ void get_batched_kernels(int bits, bool serial, bool sym, const void** prepare, 
 cudaError_t launch_graph_pairs(const uint32_t* mate, const int64_t* vbase, uint64_t num_graphs,
                                uint64_t n, uint64_t* graph_pairs, int grid, cudaStream_t s);
 
+// batch.cu: batched Skipper with a partition per member graph (local ids,
+// warps-per-graph cap); every table is computed on the device
+struct BatchParams {
+  SweepParams P;           // the whole batch: n, nnz, offsets, nbrs, state, mate, work, err, spin_limit
+  const int64_t* vbase;    // [G+1] first vertex of each graph
+  const int64_t* ebase;    // [G+1] first entry of each graph
+  uint64_t num_graphs;
+  uint64_t* ubase;         // [G+1] first work unit of each graph (made on the device)
+  uint64_t* sbase;         // [G+1] first state word of each graph (local ids, packed layouts)
+  uint64_t* totals;        // [2]: units, state words
+  uint32_t* gid;           // graph of each unit
+  int64_t* part;           // per unit: first row (view coordinates), first entry (batch index)
+  uint64_t grain;          // rows + entries per unit
+  uint32_t wpg;            // most units per graph, 0 = no cap
+  uint32_t local;          // 1: member graphs hold local ids
+  uint64_t* graph_pairs;   // [G] matched pairs per graph, or null
+};
+struct BatchKernels {
+  const void* plan;        // <<<1, batch_plan_threads()>>>(BatchParams)
+  const void* prepare;     // (BatchParams, int states)
+  const void* sweep;       // (BatchParams); the serial kernel takes one thread per graph
+  const void* pairs;       // (BatchParams)
+};
+void get_batch_kernels(int bits, bool local, bool serial, bool sym, BatchKernels* k);
+int batch_sweep_blocks_per_sm(int bits, bool local, bool sym, int block_threads);
+int batch_plan_threads();
+// one verdict for the whole batch in 9 counters (mm_verdict order after flags)
+cudaError_t launch_validate_batch(const BatchParams& B, unsigned long long* counters, int grid,
+                                  cudaStream_t s);
+
 // coo.cu: Skipper over an edge list (src[i], dst[i]) in coordinate form
 struct CooParams {
   SweepParams P;        // n, state, mate, work, err, spin_limit, poison, stats (CSR fields unused)

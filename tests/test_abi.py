@@ -58,7 +58,8 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(mm_stats), offsetof(mm_stats, transitions),
          offsetof(mm_stats, illegal_transitions), offsetof(mm_stats, id_loads_open),
          offsetof(mm_options, id_loads), (size_t)MM_ID_LOADS_SELECTIVE);
-  printf("%zu %zu\n", offsetof(mm_options, stage_windows), offsetof(mm_options, reserved));
+  printf("%zu %zu %zu %u\n", offsetof(mm_options, stage_windows), offsetof(mm_options, reserved),
+         offsetof(mm_options, warps_per_graph), MM_BATCH_LOCAL_IDS);
   return 0;
 }
 """
@@ -76,7 +77,8 @@ int main(void) {
                     ctypes.sizeof(R), R.verdict.offset, R.done_ns.offset, ctypes.sizeof(G),
                     ctypes.sizeof(native.Stats), native.Stats.transitions.offset,
                     native.Stats.illegal_transitions.offset, native.Stats.id_loads_open.offset,
-                    O.id_loads.offset, 2, O.stage_windows.offset, O.reserved.offset]
+                    O.id_loads.offset, 2, O.stage_windows.offset, O.reserved.offset,
+                    O.warps_per_graph.offset, 4]
 
 
 def test_default_options_and_argument_errors(native):
@@ -94,6 +96,10 @@ def test_default_options_and_argument_errors(native):
                              ctypes.byref(h)) == 1   # nbrs not 16-byte aligned
     assert b"aligned" in lib.mm_last_error()
     assert lib.mm_create_csr(1 << 33, 0, ctypes.c_void_p(64), None, 0, None, ctypes.byref(h)) == 1
+    # a local-id batch takes no device check and no host mapping, and its n has a ceiling too
+    assert lib.mm_create_csr(4, 4, ctypes.c_void_p(64), ctypes.c_void_p(64), 4 | 1, None, ctypes.byref(h)) == 6
+    assert lib.mm_create_csr(4, 4, ctypes.c_void_p(64), ctypes.c_void_p(64), 4 | 2, None, ctypes.byref(h)) == 6
+    assert lib.mm_create_csr((1 << 40) + 1, 0, ctypes.c_void_p(64), None, 4, None, ctypes.byref(h)) == 1
     assert lib.mm_skipper(None, None, None, None, 0, None, None) == 1
     assert lib.mm_destroy(None) == 0
     assert lib.mm_version().startswith(b"skipper-gb300")
