@@ -440,6 +440,99 @@ def run_batched(args, skp):
 
 
 # ----------------------------------------------------------------------------
+# the other scale-27 graphs: uniform and high-skew R-MAT, every state layout
+# ----------------------------------------------------------------------------
+def time_sweep(h, mate, opts, steps, warmup):
+    """Device time per call and mean init / sweep kernel times of `steps`
+    back-to-back calls (CUDA events on the launching stream)."""
+    import torch
+    for _ in range(max(3, warmup)):
+        h.skipper(mate=mate, opts=opts)
+    h.sync()
+    h.timing_history()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        h.skipper(mate=mate, opts=opts)
+    e1.record()
+    torch.cuda.synchronize()
+    h.sync()
+    hist = h.timing_history(256)
+    return (e0.elapsed_time(e1) / steps, statistics.mean(t["sweep_ms"] for t in hist),
+            statistics.mean(t["init_ms"] for t in hist))
+
+
+def run_side_graphs(args, skp, m_headline):
+    """Config C3's companions of the headline graph: a uniform random graph with
+    the same n and edge draws, and a high-skew R-MAT (a = .7, b = c = d = .1),
+    each timed in the byte, 2-bit and 32-bit state layouts (and the 2-bit
+    layout with symmetric = 1), with the same roofline arithmetic as the
+    headline line."""
+    import graphgen as gg
+    import torch
+    scale, ef = args.scale, args.edge_factor
+    n = 1 << scale
+    chunks = (16 << max(0, scale - 27)) if scale >= 26 else 1
+    peak, peak_kind = measured_peaks()
+    gens = {
+        f"uniform{scale}": (lambda: gg.uniform(n, m_headline, seed=args.seed, device="cuda", chunks=chunks),
+                            f"{m_headline} uniform random pairs on 2^{scale} vertices (the headline R-MAT's n "
+                            "and undirected m), loops and repeats dropped, symmetrised"),
+        f"rmat{scale}_skew": (lambda: gg.rmat(scale, ef, 0.7, 0.1, 0.1, seed=args.seed, device="cuda",
+                                              chunks=chunks),
+                              f"R-MAT scale {scale}, edge factor {ef}, a/b/c/d=.7/.1/.1/.1, ids permuted, "
+                              "symmetrised, deduplicated"),
+    }
+    out = {}
+    for name, (gen, desc) in gens.items():
+        t = time.time()
+        g = gen()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        log(f"{name}: n={g.n} nnz={g.nnz} generated in {time.time() - t:.1f}s")
+        sweep_bytes = 8 * (g.n + 1) + 4 * g.nnz
+        res = {"workload": desc, "n": g.n, "nnz": g.nnz, "grain": args.grain, "block_threads": args.block,
+               "l2": "inputs larger than L2 (CSR %.1f GB); no flush" % (sweep_bytes / 1e9), "layouts": {}}
+        mate = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        with skp.Graph(g.offsets, g.nbrs, check=True) as h:
+            for bits, sym in ((8, 0), (2, 0), (32, 0), (2, 1)):
+                o = skp.options(status_bits=bits, grain=args.grain, block_threads=args.block, nosync=1,
+                                timing=1, symmetric=sym)
+                ms, sweep_ms, init_ms = time_sweep(h, mate, o, args.side_steps, args.warmup)
+                v = h.validate(mate)
+                if v.flags != 0:
+                    raise SystemExit(f"invalid matching on {name} (bits {bits}): {v.as_dict()}")
+                s = {2: 0.25, 8: 1.0, 32: 4.0}[bits]
+                step_bytes = int(8 * (g.n + 1) + 4 * g.nnz + s * g.n + (4 * g.n if bits != 32 else 0))
+                achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9
+                res["layouts"][f"u{bits}" + ("_symmetric" if sym else "")] = {
+                    "ms_per_step": ms, "sweep_ms": sweep_ms, "init_ms": init_ms,
+                    "value": g.nnz / (ms * 1e-3) / 1e9, "unit": UNIT,
+                    "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                 "frac": achieved / peak,
+                                 "traffic": None if sym else ncu_traffic(name, bits),
+                                 "bytes_per_launch": sweep_bytes,
+                                 "kernel": f"sweep_kernel<{ {2: 'TwoBit', 8: 'Byte', 32: 'Word'}[bits]}State>",
+                                 "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
+                                 "step_bytes_alg": step_bytes,
+                                 "step_frac": step_bytes / (ms * 1e-3) / 1e9 / peak},
+                    "verdict": {"flags": v.flags, "n_pairs": v.n_pairs}}
+            h.skipper(mate=mate, status_bits=8, grain=args.grain, block_threads=args.block, stats=1)
+            st = h.stats()
+            res["stats_u8"] = {k: st[k] for k in ("entries_read", "windows", "chunks", "attempts", "matches",
+                                                   "conflicts", "id_loads", "id_loads_open")}
+            res["stats_u8"]["ids_read_frac"] = st["entries_read"] / max(1, g.nnz)
+        best = max(res["layouts"].items(), key=lambda kv: kv[1]["value"])
+        res["best_layout"] = best[0]
+        out[name] = res
+        del g, mate
+        torch.cuda.empty_cache()
+    return out
+
+
+# ----------------------------------------------------------------------------
 # served: Poisson request stream through the continuous-batching server
 # ----------------------------------------------------------------------------
 # ----------------------------------------------------------------------------
@@ -571,6 +664,33 @@ def run_served(args, skp, min_edges=None, max_edges=None, seconds=None, rate=Non
                             "on two alternating compute streams, mm_validate_multi before completion, "
                             "D2H on a second copy stream into a result buffer per pool graph (reused, "
                             "as the serial run does)"}
+    # the trace's copy ceiling: each pool graph's CSR copied host -> device
+    # (pinned, one stream, no kernel), timed, and summed over the requests
+    big = max(x[3] for x in pool)
+    d_off = torch.empty(max(x[2] for x in pool) + 1, dtype=torch.int64, device="cuda")
+    d_nb = torch.empty(max(big, 4), dtype=torch.int32, device="cuda")
+    t_copy = []
+    for off, nb, n, nnz in pool:
+        ts = []
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            d_off[: n + 1].copy_(off, non_blocking=True)
+            d_nb[:nnz].copy_(nb, non_blocking=True)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        t_copy.append(statistics.median(ts))
+    del d_off, d_nb
+    ceil_s = float(sum(t_copy[p] for p in picks))
+    ceil_bytes = int(sum(8 * (pool[p][2] + 1) + 4 * pool[p][3] for p in picks))
+    out["copy_ceiling"] = {"gedges_s": entries / ceil_s / 1e9, "seconds": ceil_s,
+                           "link_gbs": ceil_bytes / ceil_s / 1e9, "bytes": ceil_bytes,
+                           "served_frac": out["served"]["gedges_s"] / (entries / ceil_s / 1e9),
+                           "how": "every pool graph's CSR copied host -> device from pinned memory on one "
+                                  "stream with no kernel (median of 3, CUDA events), summed over the "
+                                  "trace's requests: the rate at which the link alone could deliver them"}
     if not serial:
         return out
     # serial plain: one request at a time through the plain API, in arrival order

@@ -64,3 +64,26 @@ def test_committed_profiles_parse():
     for name in read:
         text = open(os.path.join(bench.ROOT, "profiles", name)).read()
         assert "kernel_source_sha256_16:" in text and "dram_bytes_per_launch:" in text, name
+
+
+def test_every_global_name_bench_uses_is_defined():
+    """bench.py runs its GPU legs only on a GPU machine; a name it calls but no
+    longer defines would surface there first, so check the module here."""
+    import ast
+    import builtins
+    src = open(bench.__file__).read()
+    tree = ast.parse(src)
+    defined = set(dir(builtins)) | set(vars(bench))
+    used = set()
+    local = set()
+    for node in ast.walk(tree):
+        if isinstance(node, ast.Name):
+            (used if isinstance(node.ctx, ast.Load) else local).add(node.id)
+        elif isinstance(node, (ast.FunctionDef, ast.arg)):
+            local.add(node.name if isinstance(node, ast.FunctionDef) else node.arg)
+        elif isinstance(node, (ast.Import, ast.ImportFrom)):
+            local.update((a.asname or a.name).split(".")[0] for a in node.names)
+        elif isinstance(node, ast.ExceptHandler) and node.name:
+            local.add(node.name)
+    missing = sorted(used - defined - local)
+    assert not missing, missing
