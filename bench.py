@@ -371,8 +371,54 @@ def run_batched(args, skp):
     parts = [gg.unpack(packed, g) for g in range(G)]
     mates = [torch.empty(p.n, dtype=torch.int32, device="cuda") for p in parts]
     handles = [skp.Graph(p.offsets, p.nbrs, check=False) for p in parts]
-    o = skp.options(status_bits=tuned.status_bits, grain=tuned.grain,
-                    block_threads=tuned.block_threads, nosync=1)
+    def plain_replay(opts):
+        """The 4096 calls captured once into a CUDA graph and replayed: one launch
+        sequence per graph with no host work between them (median of 3, ms)."""
+        for hg, m in zip(handles, mates):
+            hg.skipper(mate=m, opts=opts)
+        torch.cuda.synchronize()
+        cg = torch.cuda.CUDAGraph()
+        s_cap = torch.cuda.Stream()
+        s_cap.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s_cap):
+            with torch.cuda.graph(cg, stream=s_cap):
+                for hg, m in zip(handles, mates):
+                    hg.skipper(mate=m, opts=opts)
+        torch.cuda.synchronize()
+        cg.replay()
+        torch.cuda.synchronize()
+        rt = []
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            cg.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            rt.append(e0.elapsed_time(e1))
+        del cg
+        return statistics.median(rt)
+
+    # the plain arm gets its own settings: the grain and state layout that make
+    # one call per graph fastest (a batch-sized grain leaves a small graph to a
+    # few warps)
+    search = {}
+    for grain in (128, 512, 2048, 8192):
+        for bits in (2, 8):
+            o_try = skp.options(status_bits=bits, grain=grain, block_threads=512, nosync=1)
+            try:
+                search[f"grain{grain}_u{bits}"] = plain_replay(o_try)
+            except Exception as e:   # capture refused: no replay figures
+                log("plain arm graph capture failed:", e)
+                torch.cuda.synchronize()
+                break
+    best_key = min(search, key=search.get) if search else None
+    if best_key:
+        gbest, bbest = int(best_key[5:best_key.index("_")]), int(best_key[best_key.index("_u") + 2:])
+    else:
+        gbest, bbest = 512, tuned.status_bits
+    o = skp.options(status_bits=bbest, grain=gbest, block_threads=512, nosync=1)
+    replay = search.get(best_key) if best_key else None
     for hg, m in zip(handles, mates):
         hg.skipper(mate=m, opts=o)
     torch.cuda.synchronize()
@@ -391,34 +437,6 @@ def run_batched(args, skp):
         lat.append((time.perf_counter() - t0) * 1e3)
         torch.cuda.synchronize()
         span.append(e0.elapsed_time(e1))
-    # the same 4096 calls captured once into a CUDA graph and replayed: one
-    # launch per graph with no host work between the launches
-    replay = None
-    try:
-        cg = torch.cuda.CUDAGraph()
-        s_cap = torch.cuda.Stream()
-        s_cap.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(s_cap):
-            with torch.cuda.graph(cg, stream=s_cap):
-                for hg, m in zip(handles, mates):
-                    hg.skipper(mate=m, opts=o)
-        torch.cuda.synchronize()
-        cg.replay()
-        torch.cuda.synchronize()
-        rt = []
-        for _ in range(5):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            cg.replay()
-            e1.record()
-            torch.cuda.synchronize()
-            rt.append(e0.elapsed_time(e1))
-        replay = statistics.median(rt)
-        del cg
-    except Exception as e:   # capture refused: report the two other timings only
-        log("plain arm graph capture failed:", e)
-        torch.cuda.synchronize()
     bad = sum(handles[g].validate(mates[g]).flags != 0 for g in range(0, G, max(1, G // 64)))
     if bad:
         raise SystemExit("invalid per-graph matching")
@@ -428,11 +446,14 @@ def run_batched(args, skp):
                plain_gedges_s=csr.nnz / (pct(lat, 50) * 1e-3) / 1e9,
                plain_device_span_ms=statistics.median(span),
                plain_graph_replay_ms=replay,
+               plain_settings={"grain": gbest, "status_bits": bbest, "block_threads": 512,
+                               "replay_ms_by_setting": search},
                plain_how="one mm_skipper call per graph (nosync; init + sweep launches and a 4-byte "
-                         "status copy each, grids sized to the graph), then one status read per graph; "
-                         "wall = host time of the loop; device span = CUDA events around the launches; "
-                         "graph replay = the same calls captured once into a CUDA graph (no host work "
-                         "between launches)",
+                         "status copy each, grids sized to the graph), then one status read per graph, "
+                         "with the grain and layout that make the replayed loop fastest; wall = host "
+                         "time of the loop; device span = CUDA events around the launches; graph replay "
+                         "= the same calls captured once into a CUDA graph (no host work between "
+                         "launches)",
                speedup_vs_plain=pct(lat, 50) / out["p50_ms"],
                speedup_vs_plain_device_span=statistics.median(span) / out["p50_ms"],
                speedup_vs_plain_graph_replay=(replay / out["p50_ms"]) if replay else None)

@@ -408,9 +408,12 @@ mm_status mm_timing_history(mm_graph *g, mm_timing *out, uint32_t max, uint32_t 
  * Autotuner for mm_skipper_batched: times the candidate settings -- grain in
  * {1024, 2048, 4096, 8192}, status_bits in {2, 8, 32}, block_threads in {256,
  * 512}, warps_per_graph in {0 (no cap), 1, 4, 16} -- on this batch with CUDA
- * events, keeps the fastest whose result passes the device checker
- * (mm_validate_batched), and writes it into *o (other fields of *o are kept).
- * d_mate_scratch: uint32_t[n].  Synchronous.
+ * events: one untimed and three timed runs each, a candidate whose first timed
+ * run is already 1.5x slower than the best run so far being dropped.  Every
+ * new best is checked by the device checker (mm_validate_batched; an invalid
+ * result fails the call with MM_ERR_CUDA), and the fastest is written into
+ * *o (other fields of *o are kept).  d_mate_scratch: uint32_t[n].
+ * Synchronous.
  */
 mm_status mm_autotune_batched(mm_graph *g, uint64_t num_graphs, const int64_t *d_vbase,
                               const int64_t *d_ebase, uint32_t *d_mate_scratch,

@@ -1169,25 +1169,34 @@ mm_status mm_autotune_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d
         c.use_graph = 0;
         c.nosync = 0;
         c.timing = 1;
+        // one untimed run, one timed run; a candidate already 1.5x slower than
+        // the best per run is dropped, the others get two more timed runs
         float total = 0;
+        int reps = 0;
+        bool dropped = false;
         for (int rep = 0; rep < 4; ++rep) {
           if ((st = mm_skipper_batched(g, num_graphs, d_vbase, d_ebase, &c, d_mate_scratch, nullptr, s)) != MM_OK)
             return st;
           mm_timing t;
           if ((st = mm_get_timing(g, &t)) != MM_OK) return st;
-          if (rep > 0) total += t.total_ms;
+          if (rep == 0) continue;
+          total += t.total_ms;
+          ++reps;
+          if (rep == 1 && best < 1e30f && t.total_ms > 1.5f * (best / 3.0f)) {
+            dropped = true;
+            break;
+          }
         }
+        if (dropped || reps != 3 || total >= best) continue;
         mm_verdict v;
         if ((st = mm_validate_batched(g, num_graphs, d_vbase, d_ebase, d_mate_scratch, &v, s)) != MM_OK) return st;
         if (v.flags) return fail(MM_ERR_CUDA, "autotune candidate gave an invalid matching (flags 0x%x)", v.flags);
-        if (total < best) {
-          best = total;
-          best_o = *o;
-          best_o.grain = gr;
-          best_o.status_bits = sb;
-          best_o.block_threads = bt;
-          best_o.warps_per_graph = wg;
-        }
+        best = total;
+        best_o = *o;
+        best_o.grain = gr;
+        best_o.status_bits = sb;
+        best_o.block_threads = bt;
+        best_o.warps_per_graph = wg;
         }
   *o = best_o;
   return MM_OK;
