@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--no-side-graphs", action="store_true",
                     help="skip the uniform and high-skew graphs of the headline's size")
     ap.add_argument("--side-steps", type=int, default=10)
+    ap.add_argument("--layout-steps", type=int, default=20,
+                    help="steps for the headline graph in the 2- and 32-bit layouts (0 = skip)")
     ap.add_argument("--served-in-place-max-nnz", type=int, default=1 << 20)
     ap.add_argument("--symmetric-steps", type=int, default=50)
     ap.add_argument("--edge-list-steps", type=int, default=20)
@@ -849,6 +851,27 @@ def run_ours(args):
                             "sweep tests each edge once, from its lower endpoint's row; same graph, "
                             "same launch, edges counted as stored entries like the headline"}
 
+    # the same graph in the other state layouts (and the byte layout with the
+    # 32-register instance), timed the same way: the library's choices beside
+    # the paper's one byte per vertex
+    layouts = {}
+    if args.layout_steps > 0:
+        for name, kw in (("u2", dict(status_bits=2)), ("u32", dict(status_bits=32)),
+                         ("u8_64warps", dict(status_bits=8, blocks_per_sm=4))):
+            o_l = skp.options(grain=args.grain, block_threads=args.block, nosync=1, timing=1, **kw)
+            ms_l, sw_l, _ = time_sweep(h, mate, o_l, args.layout_steps, args.warmup)
+            v_l = h.validate(mate)
+            if v_l.flags != 0:
+                raise SystemExit(f"invalid matching ({name}): {v_l.as_dict()}")
+            a_l = sweep_bytes / (sw_l * 1e-3) / 1e9
+            s_l = {"u2": 0.25, "u32": 4.0, "u8_64warps": 1.0}[name]
+            sb_l = int(8 * (n + 1) + 4 * nnz + s_l * n + (4 * n if name != "u32" else 0))
+            layouts[name] = {"value": job_gedges(world, nnz, max_over_ranks(ms_l, dist) * 1e-3), "unit": UNIT,
+                             "ms_per_step": ms_l, "sweep_ms": sw_l, "roofline_frac": a_l / peak,
+                             "step_frac": sb_l / (ms_l * 1e-3) / 1e9 / peak,
+                             "verdict": {"flags": v_l.flags, "n_pairs": v_l.n_pairs},
+                             "options": {k: int(v) for k, v in kw.items()}}
+
     # end to end through the public API with host buffers: the host session
     # reads the pinned host CSR in place (MM_HOST_MAPPED, over NVLink-C2C), and,
     # beside it, the copy path (whole CSR host -> device, then the same call)
@@ -997,6 +1020,7 @@ def run_ours(args):
         "kernel_ms": {"init": init_ms, "sweep": sweep_ms},
         "verdict": {"flags": v_end.flags, "n_pairs": v_end.n_pairs},
         "symmetric_option": symmetric,
+        "layouts": layouts,
         "side_graphs": side,
         "edge_list": edge_list,
         "batched": batched,

@@ -84,7 +84,17 @@ typedef struct mm_options {
                                 0 = 2048.  Must be a multiple of 128 when set. */
     uint32_t block_threads;  /* sweep threads per block, multiple of 32, <= 512;
                                 0 = 512 */
-    uint32_t blocks_per_sm;  /* sweep blocks per SM; 0 = the occupancy maximum */
+    uint32_t blocks_per_sm;  /* sweep blocks per SM; 0 = the occupancy maximum of the
+                                instance the layout uses by default.  The plain and
+                                symmetric CSR sweeps (single graph and batched) come
+                                in two instances: compiled for 40 registers a thread
+                                (3 blocks of 512 threads, 48 warps per SM; the
+                                default for 8- and 32-bit states) and for 32 (4
+                                blocks of 512, 64 warps per SM; the default for
+                                2-bit states, whose array stays in L2, so more
+                                warps hide more latency).  A value above what the
+                                40-register instance fits selects the 32-register
+                                one. */
     uint32_t nosync;         /* 1: return without waiting for the GPU; the status
                                 of the work (timeout, bad id) is read by mm_sync() */
     uint32_t timing;         /* 1: record CUDA events around each kernel on the
@@ -406,8 +416,10 @@ mm_status mm_timing_history(mm_graph *g, mm_timing *out, uint32_t max, uint32_t 
 
 /*
  * Autotuner for mm_skipper_batched: times the candidate settings -- grain in
- * {1024, 2048, 4096, 8192}, status_bits in {2, 8, 32}, block_threads in {256,
- * 512}, warps_per_graph in {0 (no cap), 1, 4, 16} -- on this batch with CUDA
+ * {1024, 2048, 4096, 8192}, status_bits in {2, 8, 32}, block_threads 512 with
+ * blocks_per_sm either the 40-register instance's or the 32-register
+ * instance's occupancy (see blocks_per_sm), warps_per_graph in {0 (no cap), 4,
+ * 16} -- on this batch with CUDA
  * events: one untimed and three timed runs each, a candidate whose first timed
  * run is already 1.5x slower than the best run so far being dropped.  Every
  * new best is checked by the device checker (mm_validate_batched; an invalid

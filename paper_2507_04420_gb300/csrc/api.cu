@@ -125,6 +125,7 @@ struct Resolved {
   int blocks_per_sm;
   bool nosync, timing, use_graph, l2_persist, stats, sym, sel, stage;
   uint32_t wpg;
+  bool lean;          // the 32-register instance of the plain / symmetric sweep
   uint64_t spin_limit, poison;
 };
 
@@ -155,6 +156,7 @@ mm_status resolve(const mm_graph* g, const mm_options* o, Resolved* r) {
   r->sel = o->id_loads == MM_ID_LOADS_SELECTIVE || (o->id_loads == MM_ID_LOADS_AUTO && g->host_mapped);
   r->stage = o->stage_windows != 0;
   r->wpg = o->warps_per_graph;
+  r->lean = sweep_lean(r->bits, r->block, r->blocks_per_sm);
   r->spin_limit = o->spin_limit ? o->spin_limit : kDefaultSpin;
   r->poison = o->poison_vertex;
   if (r->poison > g->n) return fail(MM_ERR_ARG, "poison_vertex out of range");
@@ -172,8 +174,9 @@ mm_status ensure_part(mm_graph* g, uint64_t units) {
   return MM_OK;
 }
 
-int sweep_grid(const mm_graph* g, const Resolved& r) {
-  const int per_sm = r.blocks_per_sm > 0 ? r.blocks_per_sm : sweep_blocks_per_sm(r.bits, r.block);
+// the persistent grid of a CSR sweep; `lean`: the 32-register instance runs
+int sweep_grid(const mm_graph* g, const Resolved& r, bool lean) {
+  const int per_sm = r.blocks_per_sm > 0 ? r.blocks_per_sm : sweep_blocks_per_sm(r.bits, r.block, lean);
   return g->num_sms * per_sm;
 }
 
@@ -188,10 +191,10 @@ int prepare_grid_for(const mm_graph* g, uint64_t units) {
   const uint64_t blocks = (items + 255) / 256;
   return blocks < (uint64_t)prepare_grid(g) ? (int)blocks : prepare_grid(g);
 }
-int sweep_grid_for(const mm_graph* g, const Resolved& r, uint64_t units) {
+int sweep_grid_for(const mm_graph* g, const Resolved& r, bool lean, uint64_t units) {
   const uint64_t warps = (uint64_t)(r.block / 32);
   const uint64_t blocks = (units + warps - 1) / warps;
-  const int full = sweep_grid(g, r);
+  const int full = sweep_grid(g, r, lean);
   return blocks < (uint64_t)full ? (int)(blocks ? blocks : 1) : full;
 }
 
@@ -216,6 +219,8 @@ SweepParams make_params(mm_graph* g, const Resolved& r, uint32_t* d_mate) {
   const bool aligned16 = ((reinterpret_cast<uintptr_t>(g->offsets) |
                            reinterpret_cast<uintptr_t>(P.state)) & 15u) == 0;
   P.tile = r.stage && !r.serial && !r.word && !g->host_mapped && aligned16;
+  // the 32-register instance exists for the plain and symmetric sweeps only
+  P.lean = r.lean && !r.serial && !r.stats && !P.sel && !P.tile;
   return P;
 }
 
@@ -609,7 +614,7 @@ mm_status mm_skipper(mm_graph* g, const mm_options* o, uint32_t* d_mate, uint32_
   L2Window win;
   if (!r.serial) {
     if ((st = win.open(g, r, s, P.state, r.word ? g->n * 4 : packed_words(g->n, r.bits) * 4)) != MM_OK) return st;
-    CUDA_TRY(launch_sweep(P, r.bits, sweep_grid_for(g, r, units), r.block, s));
+    CUDA_TRY(launch_sweep(P, r.bits, sweep_grid_for(g, r, P.lean != 0, units), r.block, s));
     if ((st = win.close()) != MM_OK) return st;
   } else {
     CUDA_TRY(launch_serial(P, r.bits, s));
@@ -689,7 +694,7 @@ mm_status build_batch_graph(mm_graph* g, const Resolved& r, uint64_t num_graphs,
   b = BatchGraph{};
   CUDA_TRY(cudaGraphCreate(&b.graph, 0));
   const void *k_prepare = nullptr, *k_sweep = nullptr, *k_pairs = nullptr;
-  get_batched_kernels(r.bits, r.serial, P.sym != 0, &k_prepare, &k_sweep, &k_pairs);
+  get_batched_kernels(r.bits, r.serial, P.sym != 0, P.lean != 0, &k_prepare, &k_sweep, &k_pairs);
 
   SweepParams p = P;
   uint64_t* gp = graph_pairs;
@@ -709,7 +714,7 @@ mm_status build_batch_graph(mm_graph* g, const Resolved& r, uint64_t num_graphs,
     ks.gridDim = dim3((unsigned)((num_graphs + 127) / 128));
     ks.blockDim = dim3(128);
   } else {
-    ks.gridDim = dim3(sweep_grid(g, r));
+    ks.gridDim = dim3(sweep_grid(g, r, P.lean != 0));
     ks.blockDim = dim3(r.block);
   }
   ks.kernelParams = sweep_args;
@@ -749,7 +754,7 @@ mm_status update_batch_graph(mm_graph* g, const Resolved& r, uint64_t num_graphs
                              const SweepParams& P, uint64_t* graph_pairs) {
   BatchGraph& b = g->bg;
   const void *k_prepare = nullptr, *k_sweep = nullptr, *k_pairs = nullptr;
-  get_batched_kernels(r.bits, r.serial, P.sym != 0, &k_prepare, &k_sweep, &k_pairs);
+  get_batched_kernels(r.bits, r.serial, P.sym != 0, P.lean != 0, &k_prepare, &k_sweep, &k_pairs);
   SweepParams p = P;
   uint64_t* gp = graph_pairs;
   uint64_t ng = num_graphs;
@@ -852,7 +857,8 @@ struct BatchLaunch {
 
 BatchLaunch batch_launch(const mm_graph* g, const Resolved& r, uint64_t num_graphs) {
   BatchLaunch L{};
-  get_batch_kernels(r.bits, g->local_ids, r.serial, r.sym && !r.serial, &L.k);
+  const bool lean = r.lean && !r.serial;
+  get_batch_kernels(r.bits, g->local_ids, r.serial, r.sym && !r.serial, lean, &L.k);
   L.plan_grid = dim3(1);
   L.plan_block = dim3(batch_plan_threads());
   L.prep_grid = dim3(prepare_grid(g));
@@ -862,7 +868,7 @@ BatchLaunch batch_launch(const mm_graph* g, const Resolved& r, uint64_t num_grap
     L.sweep_block = dim3(128);
   } else {
     const int per_sm = r.blocks_per_sm > 0 ? r.blocks_per_sm
-                                           : batch_sweep_blocks_per_sm(r.bits, g->local_ids, r.sym, r.block);
+                                           : batch_sweep_blocks_per_sm(r.bits, g->local_ids, r.sym, lean, r.block);
     L.sweep_grid = dim3(g->num_sms * per_sm);
     L.sweep_block = dim3(r.block);
   }
@@ -1044,7 +1050,7 @@ mm_status mm_skipper_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d_
   if (r.serial)
     CUDA_TRY(launch_serial_batched(P, r.bits, s));
   else
-    CUDA_TRY(launch_sweep(P, r.bits, sweep_grid(g, r), r.block, s));
+    CUDA_TRY(launch_sweep(P, r.bits, sweep_grid(g, r, P.lean != 0), r.block, s));
   if (ev) CUDA_TRY(cudaEventRecord(ev[2], s));
   if (d_graph_pairs)
     CUDA_TRY(launch_graph_pairs(d_mate, d_vbase, num_graphs, g->n, d_graph_pairs, prepare_grid(g), s));
@@ -1151,19 +1157,22 @@ mm_status mm_autotune_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d
   if (g->coo) return fail(MM_ERR_UNSUPPORTED, "batched calls take a CSR handle");
   static const uint32_t grains[] = {1024, 2048, 4096, 8192};
   static const uint32_t bits[] = {2, 8, 32};
-  static const uint32_t blocks[] = {256, 512};
-  static const uint32_t wpgs[] = {0, 1, 4, 16};
+  static const uint32_t wpgs[] = {0, 4, 16};
+  const uint32_t bt = 512;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   float best = 1e30f;
   mm_options best_o = *o;
   for (uint32_t gr : grains)
     for (uint32_t sb : bits)
-      for (uint32_t bt : blocks)
+      for (int lean = 0; lean < 2; ++lean)
         for (uint32_t wg : wpgs) {
+        // occupancy: the blocks per SM of the 40- or the 32-register instance
+        const uint32_t bps = (uint32_t)sweep_blocks_per_sm((int)sb, (int)bt, lean != 0);
         mm_options c = *o;
         c.grain = gr;
         c.status_bits = sb;
         c.block_threads = bt;
+        c.blocks_per_sm = bps;
         c.warps_per_graph = wg;
         c.serial = 0;
         c.use_graph = 0;
@@ -1196,6 +1205,7 @@ mm_status mm_autotune_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d
         best_o.grain = gr;
         best_o.status_bits = sb;
         best_o.block_threads = bt;
+        best_o.blocks_per_sm = bps;
         best_o.warps_per_graph = wg;
         }
   *o = best_o;

@@ -193,8 +193,8 @@ __global__ void batch_prepare_kernel(BatchParams B, int states) {
   }
 }
 
-template <class S, bool kLocal, bool kSym>
-__global__ void __launch_bounds__(512, 3) batch_sweep_kernel(BatchParams B) {
+template <class S, bool kLocal, bool kSym, bool kLean>
+__global__ void __launch_bounds__(512, kLean ? 4 : 3) batch_sweep_kernel(BatchParams B) {
   constexpr bool kWord = S::kPerWord == 1;
   const unsigned lane = threadIdx.x & 31u;
   const uint64_t pol = policy_evict_first();
@@ -371,7 +371,7 @@ __global__ void batch_check_vertices_kernel(BatchParams B, unsigned long long* c
 #define SKP_BATCH_STATE(bits, F) \
   ((bits) == 32 ? F(WordState, 32) : (bits) == 2 ? F(TwoBitState, 2) : F(ByteState, 8))
 
-void get_batch_kernels(int bits, bool local, bool serial, bool sym, BatchKernels* k) {
+void get_batch_kernels(int bits, bool local, bool serial, bool sym, bool lean, BatchKernels* k) {
 #define PL(S, B) (const void*)batch_plan_kernel<B>
 #define PR(S, B) (const void*)batch_prepare_kernel<B>
   k->plan = SKP_BATCH_STATE(bits, PL);
@@ -383,18 +383,20 @@ void get_batch_kernels(int bits, bool local, bool serial, bool sym, BatchKernels
     k->sweep = SKP_BATCH_STATE(bits, SE);
 #undef SE
   } else {
-#define SW(S, B)                                                                            \
-  (local ? (sym ? (const void*)batch_sweep_kernel<S, true, true> : (const void*)batch_sweep_kernel<S, true, false>) \
-         : (sym ? (const void*)batch_sweep_kernel<S, false, true> : (const void*)batch_sweep_kernel<S, false, false>))
+#define SWL(S, L)                                                                           \
+  (local ? (sym ? (const void*)batch_sweep_kernel<S, true, true, L> : (const void*)batch_sweep_kernel<S, true, false, L>) \
+         : (sym ? (const void*)batch_sweep_kernel<S, false, true, L> : (const void*)batch_sweep_kernel<S, false, false, L>))
+#define SW(S, B) (lean ? SWL(S, true) : SWL(S, false))
     k->sweep = SKP_BATCH_STATE(bits, SW);
 #undef SW
+#undef SWL
   }
   k->pairs = local ? (const void*)batch_pairs_kernel<true> : (const void*)batch_pairs_kernel<false>;
 }
 
-int batch_sweep_blocks_per_sm(int bits, bool local, bool sym, int block_threads) {
+int batch_sweep_blocks_per_sm(int bits, bool local, bool sym, bool lean, int block_threads) {
   BatchKernels k{};
-  get_batch_kernels(bits, local, false, sym, &k);
+  get_batch_kernels(bits, local, false, sym, lean, &k);
   int b = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k.sweep, block_threads, 0) != cudaSuccess || b < 1)
     return 1;

@@ -8,14 +8,20 @@
 namespace skp {
 
 // sweep.cu (bits: 2, 8 or 32 -- the state layout, see state.cuh)
-int sweep_blocks_per_sm(int bits, int block_threads);
+// blocks of block_threads per SM that the default (lean = false) or the
+// 32-register (lean = true) instance fits
+int sweep_blocks_per_sm(int bits, int block_threads, bool lean);
+// which instance a parallel CSR sweep uses: the 32-register one when the caller
+// asks for more blocks per SM than the default fits, or by default for 2-bit
+// states (their array stays in L2, so more warps hide more latency)
+bool sweep_lean(int bits, int block_threads, int blocks_per_sm);
 cudaError_t launch_prepare(const SweepParams& P, int bits, int grid, cudaStream_t s,
                            uint64_t* graph_pairs_zero, uint64_t num_graphs);
 cudaError_t launch_sweep(const SweepParams& P, int bits, int grid, int block, cudaStream_t s);
 cudaError_t launch_serial(const SweepParams& P, int bits, cudaStream_t s);
 cudaError_t launch_serial_batched(const SweepParams& P, int bits, cudaStream_t s);
-void get_batched_kernels(int bits, bool serial, bool sym, const void** prepare, const void** sweep,
-                         const void** pairs);
+void get_batched_kernels(int bits, bool serial, bool sym, bool lean, const void** prepare,
+                         const void** sweep, const void** pairs);
 cudaError_t launch_graph_pairs(const uint32_t* mate, const int64_t* vbase, uint64_t num_graphs,
                                uint64_t n, uint64_t* graph_pairs, int grid, cudaStream_t s);
 
@@ -42,8 +48,8 @@ struct BatchKernels {
   const void* sweep;       // (BatchParams); the serial kernel takes one thread per graph
   const void* pairs;       // (BatchParams)
 };
-void get_batch_kernels(int bits, bool local, bool serial, bool sym, BatchKernels* k);
-int batch_sweep_blocks_per_sm(int bits, bool local, bool sym, int block_threads);
+void get_batch_kernels(int bits, bool local, bool serial, bool sym, bool lean, BatchKernels* k);
+int batch_sweep_blocks_per_sm(int bits, bool local, bool sym, bool lean, int block_threads);
 int batch_plan_threads();
 // one verdict for the whole batch in 9 counters (mm_verdict order after flags)
 cudaError_t launch_validate_batch(const BatchParams& B, unsigned long long* counters, int grid,

@@ -133,7 +133,8 @@ extern "C" mm_status mm_skipper_static(uint64_t n, uint64_t nnz, const int64_t* 
   if (o->serial) {
     e = launch_serial(P, 8, s);
   } else {
-    const int per_sm = o->blocks_per_sm ? (int)o->blocks_per_sm : sweep_blocks_per_sm(8, block);
+    P.lean = sweep_lean(8, block, (int)o->blocks_per_sm) ? 1u : 0u;
+    const int per_sm = o->blocks_per_sm ? (int)o->blocks_per_sm : sweep_blocks_per_sm(8, block, P.lean != 0);
     e = launch_sweep(P, 8, sms * per_sm, block, s);
   }
   if (e != cudaSuccess) return cuda_fail("sweep launch", e);

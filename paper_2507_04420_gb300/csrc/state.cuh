@@ -60,6 +60,9 @@ struct SweepParams {
   // 1: stage each 32-row window (row ends and state words) in shared memory
   // with a bulk copy one window ahead (selects the kTile kernel instance)
   uint32_t tile;
+  // 1: the plain or symmetric instance compiled for 32 registers a thread
+  // (64 warps per SM) instead of 40 (48 warps per SM)
+  uint32_t lean;
 };
 
 // Sweep statistics, kept only by the kStats kernel instances.  A conflict is a

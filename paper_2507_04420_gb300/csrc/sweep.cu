@@ -78,8 +78,13 @@ __global__ void prepare_kernel(SweepParams P, uint64_t* graph_pairs, uint64_t nu
   }
 }
 
-template <class S, bool kStats = false, bool kSym = false, bool kSel = false, bool kTile = false>
-__global__ void __launch_bounds__(512, 3) sweep_kernel(SweepParams P) {
+// Two register budgets: 40 registers a thread (3 blocks of 512 threads, 48
+// warps per SM) by default; kLean compiles for 32 (4 blocks, 64 warps per SM,
+// a few more spills), which hides more memory latency where the state array
+// stays in L2.
+template <class S, bool kStats = false, bool kSym = false, bool kSel = false, bool kTile = false,
+          bool kLean = false>
+__global__ void __launch_bounds__(512, kLean ? 4 : 3) sweep_kernel(SweepParams P) {
   const unsigned lane = threadIdx.x & 31u;
   const S s(P);
   const uint64_t pol = policy_evict_first();
@@ -154,13 +159,21 @@ __global__ void graph_pairs_kernel(const uint32_t* __restrict__ mate,
 // the same for the packed layouts only (2 or 8)
 #define SKP_DISPATCH_PACKED(bits, F) ((bits) == 2 ? F(TwoBitState, 2) : F(ByteState, 8))
 
-int sweep_blocks_per_sm(int bits, int block_threads) {
+int sweep_blocks_per_sm(int bits, int block_threads, bool lean) {
   int b = 0;
-#define OCC(S, B) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_kernel<S>, block_threads, 0)
+#define OCC(S, B)                                                                                       \
+  (lean ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_kernel<S, false, false, false, false, true>, \
+                                                        block_threads, 0)                               \
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_kernel<S>, block_threads, 0))
   cudaError_t e = SKP_DISPATCH_STATE(bits, OCC);
 #undef OCC
   if (e != cudaSuccess || b < 1) return 1;
   return b;
+}
+
+bool sweep_lean(int bits, int block_threads, int blocks_per_sm) {
+  if (blocks_per_sm > 0) return blocks_per_sm > sweep_blocks_per_sm(bits, block_threads, false);
+  return bits == 2;
 }
 
 cudaError_t launch_prepare(const SweepParams& P, int bits, int grid, cudaStream_t s,
@@ -198,11 +211,13 @@ cudaError_t launch_sweep(const SweepParams& P, int bits, int grid, int block, cu
     SKP_DISPATCH_STATE(bits, L);
 #undef L
   } else if (P.sym) {
-#define L(S, B) (sweep_kernel<S, false, true><<<grid, block, 0, s>>>(P), 0)
+#define L(S, B) (P.lean ? (sweep_kernel<S, false, true, false, false, true><<<grid, block, 0, s>>>(P), 0) \
+                        : (sweep_kernel<S, false, true><<<grid, block, 0, s>>>(P), 0))
     SKP_DISPATCH_STATE(bits, L);
 #undef L
   } else {
-#define L(S, B) (sweep_kernel<S><<<grid, block, 0, s>>>(P), 0)
+#define L(S, B) (P.lean ? (sweep_kernel<S, false, false, false, false, true><<<grid, block, 0, s>>>(P), 0) \
+                        : (sweep_kernel<S><<<grid, block, 0, s>>>(P), 0))
     SKP_DISPATCH_STATE(bits, L);
 #undef L
   }
@@ -225,12 +240,13 @@ cudaError_t launch_serial_batched(const SweepParams& P, int bits, cudaStream_t s
   return cudaGetLastError();
 }
 
-void get_batched_kernels(int bits, bool serial, bool sym, const void** prepare, const void** sweep,
-                         const void** pairs) {
+void get_batched_kernels(int bits, bool serial, bool sym, bool lean, const void** prepare,
+                         const void** sweep, const void** pairs) {
 #define PK(S, B) (const void*)prepare_kernel<B>
 #define SB(S, B) (const void*)serial_batched_kernel<S>
-#define SW(S, B) (const void*)sweep_kernel<S>
-#define SY(S, B) (const void*)sweep_kernel<S, false, true>
+#define SW(S, B) (lean ? (const void*)sweep_kernel<S, false, false, false, false, true> : (const void*)sweep_kernel<S>)
+#define SY(S, B) (lean ? (const void*)sweep_kernel<S, false, true, false, false, true> \
+                       : (const void*)sweep_kernel<S, false, true>)
   *prepare = SKP_DISPATCH_STATE(bits, PK);
   *sweep = serial ? SKP_DISPATCH_STATE(bits, SB)
                   : sym ? SKP_DISPATCH_STATE(bits, SY) : SKP_DISPATCH_STATE(bits, SW);

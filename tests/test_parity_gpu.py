@@ -118,6 +118,19 @@ def test_launch_shapes(skp, bits, block):
         assert_parity(vr, vd)
 
 
+@pytest.mark.parametrize("bits", [2, 8, 32])
+@pytest.mark.parametrize("symmetric", [0, 1])
+def test_both_register_budgets(skp, bits, symmetric):
+    """The plain and symmetric sweeps in their 40- and 32-register instances
+    (blocks_per_sm 3 and 4 of 512 threads; 0 = the layout's default), on a
+    power-law graph and on a grid, all with the oracle's verdict."""
+    for csr in (gg.rmat(14, 16, seed=12), gg.grid(200, 300)):
+        for bps in (0, 3, 4):
+            m, p, vr, vd = run(skp, csr, status_bits=bits, block_threads=512, blocks_per_sm=bps,
+                               symmetric=symmetric)
+            assert_parity(vr, vd)
+
+
 def _manual(n, rows):
     off = [0]
     nb = []
