@@ -332,10 +332,11 @@ def run_batched(args, skp):
         tune_s = time.perf_counter() - t0
         tuned.use_graph = 1
         out["tuned"] = {"grain": tuned.grain, "status_bits": tuned.status_bits,
-                        "block_threads": tuned.block_threads, "warps_per_graph": tuned.warps_per_graph,
-                        "autotune_seconds": tune_s,
-                        "searched": "grain {1024,2048,4096,8192} x status_bits {2,8,32} x block {256,512} "
-                                    "x warps_per_graph {0 (no cap),1,4,16}, each checked"}
+                        "block_threads": tuned.block_threads, "blocks_per_sm": tuned.blocks_per_sm,
+                        "warps_per_graph": tuned.warps_per_graph, "autotune_seconds": tune_s,
+                        "searched": "grain {1024,2048,4096,8192} x status_bits {2,8,32} x blocks per SM "
+                                    "{40-register instance, 32-register instance} (512 threads) x "
+                                    "warps_per_graph {0 (no cap),4,16}; every new best checked"}
         for _ in range(3):
             h.batched(packed.vbase, packed.ebase, mate=mate, opts=tuned)
         lat = []
@@ -349,7 +350,8 @@ def run_batched(args, skp):
             raise SystemExit(f"invalid batched matching: {v.as_dict()}")
         # kernel times of the same launches outside the graph (CUDA events per kernel)
         o_t = skp.options(status_bits=tuned.status_bits, grain=tuned.grain, block_threads=tuned.block_threads,
-                          warps_per_graph=tuned.warps_per_graph, timing=1, nosync=1)
+                          blocks_per_sm=tuned.blocks_per_sm, warps_per_graph=tuned.warps_per_graph, timing=1,
+                          nosync=1)
         for _ in range(3):
             h.batched(packed.vbase, packed.ebase, mate=mate, opts=o_t)
         h.sync()
