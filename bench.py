@@ -50,11 +50,16 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--scale", type=int, default=27)
+    ap.add_argument("--graph", choices=["rmat", "uniform", "skew"], default="rmat",
+                    help="the timed graph: R-MAT (.57/.19/.19/.05, the headline), uniform random pairs, "
+                         "or high-skew R-MAT (.7/.1/.1/.1); edge-factor x 2^scale draws each")
     ap.add_argument("--edge-factor", type=int, default=16)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--bits", type=int, default=8, choices=[2, 8, 32])
     ap.add_argument("--grain", type=int, default=8192)
     ap.add_argument("--block", type=int, default=512)
+    ap.add_argument("--blocks-per-sm", type=int, default=0,
+                    help="mm_options.blocks_per_sm of the timed sweep (0 = the layout's default)")
     ap.add_argument("--stage-windows", action="store_true",
                     help="mm_options.stage_windows = 1 for the timed sweep (opt-in TMA window tiles)")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -206,21 +211,33 @@ def make_graph(args, device):
     # source-range chunks bound the CSR build's temporaries (same output for any count)
     chunks = (16 << max(0, args.scale - 27)) if args.scale >= 26 else 1
     t = time.time()
-    g = gg.rmat(args.scale, args.edge_factor, 0.57, 0.19, 0.19, seed=args.seed, device=device,
-                chunks=chunks)
+    if args.graph == "uniform":
+        g = gg.uniform(1 << args.scale, args.edge_factor << args.scale, seed=args.seed, device=device,
+                       chunks=chunks)
+    else:
+        a, b, c = (0.7, 0.1, 0.1) if args.graph == "skew" else (0.57, 0.19, 0.19)
+        g = gg.rmat(args.scale, args.edge_factor, a, b, c, seed=args.seed, device=device, chunks=chunks)
     if device != "cpu":
         torch.cuda.synchronize()
-    log(f"rmat{args.scale}: n={g.n} nnz={g.nnz} generated in {time.time() - t:.1f}s")
+    log(f"{args.graph}{args.scale}: n={g.n} nnz={g.nnz} generated in {time.time() - t:.1f}s")
     if device != "cpu":
         torch.cuda.empty_cache()  # hand the generator's temporaries back
     return g
 
 
 def workload_config(args, g):
+    if args.graph == "uniform":
+        name = f"uniform{args.scale}_ef{args.edge_factor}"
+        desc = (f"{args.edge_factor} x 2^{args.scale} uniform random pairs on 2^{args.scale} vertices, loops "
+                "and repeats dropped, symmetrised; uint32 ids, int64 offsets")
+    else:
+        skew = args.graph == "skew"
+        name = f"rmat{args.scale}_ef{args.edge_factor}" + ("_skew" if skew else "")
+        desc = (f"R-MAT scale {args.scale}, edge factor {args.edge_factor}, a/b/c/d="
+                + (".7/.1/.1/.1" if skew else ".57/.19/.19/.05")
+                + ", ids permuted, symmetrised, deduplicated; uint32 ids, int64 offsets")
     return {
-        "workload": f"rmat{args.scale}_ef{args.edge_factor}",
-        "graph": f"R-MAT scale {args.scale}, edge factor {args.edge_factor}, a/b/c/d=.57/.19/.19/.05, "
-                 "ids permuted, symmetrised, deduplicated; uint32 ids, int64 offsets",
+        "workload": name, "graph": desc,
         "n": g.n, "nnz": g.nnz, "m_undirected": g.nnz // 2, "seed": args.seed,
         "edges_counted": "stored CSR entries (both directions)",
     }
@@ -765,13 +782,13 @@ def run_ours(args):
     cfg = workload_config(args, g)
     stage = 1 if args.stage_windows else 0
     opts = skp.options(status_bits=args.bits, grain=args.grain, block_threads=args.block,
-                       nosync=1, timing=1, stage_windows=stage)
+                       blocks_per_sm=args.blocks_per_sm, nosync=1, timing=1, stage_windows=stage)
     mate = torch.empty(n, dtype=torch.int32, device="cuda")
     h = skp.Graph(g.offsets, g.nbrs, check=True)
 
     # one checked run before timing: the device checker must accept it
     h.skipper(mate=mate, status_bits=args.bits, grain=args.grain, block_threads=args.block,
-              stage_windows=stage)
+              blocks_per_sm=args.blocks_per_sm, stage_windows=stage)
     verdict = h.validate(mate)
     if verdict.flags != 0:
         raise SystemExit(f"invalid matching: {verdict.as_dict()}")
@@ -816,7 +833,7 @@ def run_ours(args):
     s = {2: 0.25, 8: 1.0, 32: 4.0}[args.bits]   # state bytes per vertex
     step_bytes = int(8 * (n + 1) + 4 * nnz + s * n + (4 * n if args.bits != 32 else 0))
     # the committed counters are the default instance's
-    traffic = None if args.stage_windows else ncu_traffic(cfg["workload"], args.bits)
+    traffic = None if (args.stage_windows or args.blocks_per_sm) else ncu_traffic(cfg["workload"], args.bits)
     if args.stage_windows:
         cfg["stage_windows"] = 1
 
@@ -1010,6 +1027,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {2: "u2", 8: "u8", 32: "u32"}[args.bits], "data": "synthetic",
         "config": dict(cfg, status_bits=args.bits, grain=args.grain, block_threads=args.block,
+                       blocks_per_sm=args.blocks_per_sm or "layout default",
                        parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
                        l2="inputs larger than L2 (CSR %.1f GB vs 129 MB L2); no flush" % (sweep_bytes / 1e9)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
