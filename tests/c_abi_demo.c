@@ -6,8 +6,10 @@
  * edges 01 02 03 12 23, stored as a symmetric CSR with ascending rows.
  * Serial mode must give sequential greedy matching's result, mate = 1 0 3 2;
  * the parallel pass must give a maximal matching the checker accepts; the
- * same edges as a list must do the same; and the native server must return
- * the serial result for a host-memory request.
+ * same edges as a list must do the same; two copies of the graph packed as a
+ * batch with local ids must give that result in each copy, replayed from a
+ * CUDA graph; and the native server must return the serial result for a
+ * host-memory request.
  *
  * Prints "ok" and exits 0, or prints what failed and exits 1.
  */
@@ -83,6 +85,65 @@ int main(void)
     if ((st = mm_validate(g, d_mate, NULL, 0, &v, NULL)) != MM_OK || v.flags != 0)
         return failed("edge-list mm_validate", st);
     mm_destroy(g);
+
+    /* two copies of the graph in one batch with local ids, from a CUDA graph */
+    {
+        int64_t b_off[9];
+        uint32_t b_nb[20];
+        const int64_t b_vb[3] = {0, 4, 8}, b_eb[3] = {0, 10, 20};
+        for (int i = 0; i < 5; ++i) b_off[i] = h_off[i];
+        for (int i = 1; i < 5; ++i) b_off[4 + i] = 10 + h_off[i];
+        for (int i = 0; i < 20; ++i) b_nb[i] = h_nb[i % 10];   /* local ids in both copies */
+        int64_t *d_boff = NULL, *d_vb = NULL, *d_eb = NULL;
+        uint32_t *d_bnb = NULL, *d_bmate = NULL;
+        uint64_t *d_gp = NULL, gp[2] = {0, 0};
+        uint32_t bmate[8];
+        cudaMalloc((void **)&d_boff, sizeof b_off);
+        cudaMalloc((void **)&d_bnb, sizeof b_nb);
+        cudaMalloc((void **)&d_vb, sizeof b_vb);
+        cudaMalloc((void **)&d_eb, sizeof b_eb);
+        cudaMalloc((void **)&d_bmate, sizeof bmate);
+        cudaMalloc((void **)&d_gp, sizeof gp);
+        cudaMemcpy(d_boff, b_off, sizeof b_off, cudaMemcpyHostToDevice);
+        cudaMemcpy(d_bnb, b_nb, sizeof b_nb, cudaMemcpyHostToDevice);
+        cudaMemcpy(d_vb, b_vb, sizeof b_vb, cudaMemcpyHostToDevice);
+        cudaMemcpy(d_eb, b_eb, sizeof b_eb, cudaMemcpyHostToDevice);
+        if ((st = mm_create_csr(8, 20, d_boff, d_bnb, MM_BATCH_LOCAL_IDS, NULL, &g)) != MM_OK)
+            return failed("mm_create_csr (local ids)", st);
+        mm_default_options(&o);
+        o.serial = 1;
+        o.use_graph = 1;
+        for (int rep = 0; rep < 2; ++rep)
+            if ((st = mm_skipper_batched(g, 2, d_vb, d_eb, &o, d_bmate, d_gp, NULL)) != MM_OK)
+                return failed("mm_skipper_batched (local ids)", st);
+        cudaMemcpy(bmate, d_bmate, sizeof bmate, cudaMemcpyDeviceToHost);
+        cudaMemcpy(gp, d_gp, sizeof gp, cudaMemcpyDeviceToHost);
+        if (memcmp(bmate, expect, sizeof expect) != 0 || memcmp(bmate + 4, expect, sizeof expect) != 0 ||
+            gp[0] != 2 || gp[1] != 2) {
+            printf("local-id batch mate %u %u %u %u / %u %u %u %u, pairs %llu %llu\n", bmate[0], bmate[1],
+                   bmate[2], bmate[3], bmate[4], bmate[5], bmate[6], bmate[7], (unsigned long long)gp[0],
+                   (unsigned long long)gp[1]);
+            return 1;
+        }
+        o.serial = 0;
+        o.warps_per_graph = 1;
+        if ((st = mm_skipper_batched(g, 2, d_vb, d_eb, &o, d_bmate, NULL, NULL)) != MM_OK)
+            return failed("mm_skipper_batched (local ids, parallel)", st);
+        if ((st = mm_validate_batched(g, 2, d_vb, d_eb, d_bmate, &v, NULL)) != MM_OK) return failed("mm_validate_batched", st);
+        if (v.flags != 0 || v.n_pairs != 4) {
+            printf("local-id batch verdict flags %u pairs %llu\n", v.flags, (unsigned long long)v.n_pairs);
+            return 1;
+        }
+        if ((st = mm_skipper(g, &o, d_bmate, NULL, 0, NULL, NULL)) != MM_ERR_UNSUPPORTED)
+            return failed("mm_skipper on a local-id batch handle (expected MM_ERR_UNSUPPORTED)", st);
+        mm_destroy(g);
+        cudaFree(d_boff);
+        cudaFree(d_bnb);
+        cudaFree(d_vb);
+        cudaFree(d_eb);
+        cudaFree(d_bmate);
+        cudaFree(d_gp);
+    }
 
     /* one request through the native server, from host memory */
     mm_server_config c;
