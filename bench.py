@@ -350,10 +350,12 @@ def run_batched(args, skp):
         tuned.use_graph = 1
         out["tuned"] = {"grain": tuned.grain, "status_bits": tuned.status_bits,
                         "block_threads": tuned.block_threads, "blocks_per_sm": tuned.blocks_per_sm,
+                        "unit_order": {1: "ascending", 2: "dispersed"}.get(tuned.unit_order, "auto"),
                         "warps_per_graph": tuned.warps_per_graph, "autotune_seconds": tune_s,
                         "searched": "grain {1024,2048,4096,8192} x status_bits {2,8,32} x blocks per SM "
-                                    "{40-register instance, 32-register instance} (512 threads) x "
-                                    "warps_per_graph {0 (no cap),4,16}; every new best checked"}
+                                    "{40-register instance, 32-register instance} (512 threads) x unit order "
+                                    "{ascending, dispersed} x warps_per_graph {0 (no cap),4,16}; every new "
+                                    "best checked"}
         for _ in range(3):
             h.batched(packed.vbase, packed.ebase, mate=mate, opts=tuned)
         lat = []
@@ -367,8 +369,8 @@ def run_batched(args, skp):
             raise SystemExit(f"invalid batched matching: {v.as_dict()}")
         # kernel times of the same launches outside the graph (CUDA events per kernel)
         o_t = skp.options(status_bits=tuned.status_bits, grain=tuned.grain, block_threads=tuned.block_threads,
-                          blocks_per_sm=tuned.blocks_per_sm, warps_per_graph=tuned.warps_per_graph, timing=1,
-                          nosync=1)
+                          blocks_per_sm=tuned.blocks_per_sm, warps_per_graph=tuned.warps_per_graph,
+                          unit_order=tuned.unit_order, timing=1, nosync=1)
         for _ in range(3):
             h.batched(packed.vbase, packed.ebase, mate=mate, opts=o_t)
         h.sync()
@@ -539,9 +541,9 @@ def run_side_graphs(args, skp, m_headline):
                "l2": "inputs larger than L2 (CSR %.1f GB); no flush" % (sweep_bytes / 1e9), "layouts": {}}
         mate = torch.empty(g.n, dtype=torch.int32, device="cuda")
         with skp.Graph(g.offsets, g.nbrs, check=True) as h:
-            for bits, sym in ((8, 0), (2, 0), (32, 0), (2, 1)):
+            for bits, sym, order in ((8, 0, 0), (2, 0, 0), (32, 0, 0), (2, 1, 0), (8, 0, 2)):
                 o = skp.options(status_bits=bits, grain=args.grain, block_threads=args.block, nosync=1,
-                                timing=1, symmetric=sym)
+                                timing=1, symmetric=sym, unit_order=order)
                 ms, sweep_ms, init_ms = time_sweep(h, mate, o, args.side_steps, args.warmup)
                 v = h.validate(mate)
                 if v.flags != 0:
@@ -549,12 +551,12 @@ def run_side_graphs(args, skp, m_headline):
                 s = {2: 0.25, 8: 1.0, 32: 4.0}[bits]
                 step_bytes = int(8 * (g.n + 1) + 4 * g.nnz + s * g.n + (4 * g.n if bits != 32 else 0))
                 achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9
-                res["layouts"][f"u{bits}" + ("_symmetric" if sym else "")] = {
+                res["layouts"][f"u{bits}" + ("_symmetric" if sym else "") + ("_dispersed" if order == 2 else "")] = {
                     "ms_per_step": ms, "sweep_ms": sweep_ms, "init_ms": init_ms,
                     "value": g.nnz / (ms * 1e-3) / 1e9, "unit": UNIT,
                     "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                  "frac": achieved / peak,
-                                 "traffic": None if sym else ncu_traffic(name, bits),
+                                 "traffic": None if (sym or order) else ncu_traffic(name, bits),
                                  "bytes_per_launch": sweep_bytes,
                                  "kernel": f"sweep_kernel<{ {2: 'TwoBit', 8: 'Byte', 32: 'Word'}[bits]}State>",
                                  "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
@@ -876,14 +878,15 @@ def run_ours(args):
     layouts = {}
     if args.layout_steps > 0:
         for name, kw in (("u2", dict(status_bits=2)), ("u32", dict(status_bits=32)),
-                         ("u8_64warps", dict(status_bits=8, blocks_per_sm=4))):
+                         ("u8_64warps", dict(status_bits=8, blocks_per_sm=4)),
+                         ("u8_dispersed", dict(status_bits=8, unit_order=2))):
             o_l = skp.options(grain=args.grain, block_threads=args.block, nosync=1, timing=1, **kw)
             ms_l, sw_l, _ = time_sweep(h, mate, o_l, args.layout_steps, args.warmup)
             v_l = h.validate(mate)
             if v_l.flags != 0:
                 raise SystemExit(f"invalid matching ({name}): {v_l.as_dict()}")
             a_l = sweep_bytes / (sw_l * 1e-3) / 1e9
-            s_l = {"u2": 0.25, "u32": 4.0, "u8_64warps": 1.0}[name]
+            s_l = {"u2": 0.25, "u32": 4.0, "u8_64warps": 1.0, "u8_dispersed": 1.0}[name]
             sb_l = int(8 * (n + 1) + 4 * nnz + s_l * n + (4 * n if name != "u32" else 0))
             layouts[name] = {"value": job_gedges(world, nnz, max_over_ranks(ms_l, dist) * 1e-3), "unit": UNIT,
                              "ms_per_step": ms_l, "sweep_ms": sw_l, "roofline_frac": a_l / peak,

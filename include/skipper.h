@@ -153,8 +153,32 @@ typedef struct mm_options {
                                 time (each graph's rows + entries are split evenly
                                 over min(warps_per_graph, ceil(items / grain))
                                 units); 0 = no cap (units of `grain` items). */
-    uint64_t reserved[2];
+    uint32_t unit_order;     /* the order in which the parallel CSR sweeps (single
+                                graph and batched) hand out their work units:
+                                MM_ORDER_ASCENDING -- unit after unit from the
+                                first row, so the units in flight form one band of
+                                consecutive rows; MM_ORDER_DISPERSED -- the units
+                                are cut into as many contiguous runs as the grid
+                                has warps, and the k-th unit handed out is unit
+                                k / runs of run k mod runs, so the units in flight
+                                sit at evenly dispersed positions and each run is
+                                walked in order (the GPU form of the paper's
+                                threads that start at dispersed positions and
+                                walk contiguous runs of blocks, Section IV-C).
+                                Dispersed runs leave fewer rows unmatched when
+                                their turn comes on graphs whose rows are mostly
+                                open (uniform, grids) and cut the waits on ids
+                                with locality; the single band keeps the memory
+                                traffic of concurrent units close together.
+                                MM_ORDER_AUTO (0): dispersed for 2-bit states,
+                                ascending otherwise.  Other values: MM_ERR_ARG. */
+    uint32_t reserved32;
+    uint64_t reserved[1];
 } mm_options;
+
+#define MM_ORDER_AUTO 0u
+#define MM_ORDER_ASCENDING 1u
+#define MM_ORDER_DISPERSED 2u
 
 #define MM_ID_LOADS_AUTO 0u
 #define MM_ID_LOADS_EAGER 1u
@@ -418,8 +442,8 @@ mm_status mm_timing_history(mm_graph *g, mm_timing *out, uint32_t max, uint32_t 
  * Autotuner for mm_skipper_batched: times the candidate settings -- grain in
  * {1024, 2048, 4096, 8192}, status_bits in {2, 8, 32}, block_threads 512 with
  * blocks_per_sm either the 40-register instance's or the 32-register
- * instance's occupancy (see blocks_per_sm), warps_per_graph in {0 (no cap), 4,
- * 16} -- on this batch with CUDA
+ * instance's occupancy (see blocks_per_sm), unit_order ascending or dispersed,
+ * warps_per_graph in {0 (no cap), 4, 16} -- on this batch with CUDA
  * events: one untimed and three timed runs each, a candidate whose first timed
  * run is already 1.5x slower than the best run so far being dropped.  Every
  * new best is checked by the device checker (mm_validate_batched; an invalid
@@ -501,7 +525,7 @@ mm_status mm_destroy(mm_graph *g);
  * the reason in mm_last_error()); the grain is raised when needed so that the
  * partition fits the fixed table.  Options: status_bits 0 or 8, serial, grain,
  * block_threads, blocks_per_sm, spin_limit, poison_vertex, id_loads AUTO or
- * EAGER.  The options that need a handle's own memory -- timing, use_graph,
+ * EAGER, unit_order (ascending unless MM_ORDER_DISPERSED).  The options that need a handle's own memory -- timing, use_graph,
  * nosync, l2_persist, stats, stage_windows, symmetric and id_loads SELECTIVE
  * -- give MM_ERR_UNSUPPORTED; nothing is ignored silently.  The call waits for
  * its work and returns MM_OK, MM_ERR_TIMEOUT, MM_ERR_BAD_GRAPH, MM_ERR_ARG,

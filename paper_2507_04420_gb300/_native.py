@@ -90,7 +90,9 @@ class Options(ctypes.Structure):
         ("id_loads", ctypes.c_uint32),
         ("stage_windows", ctypes.c_uint32),
         ("warps_per_graph", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint64 * 2),
+        ("unit_order", ctypes.c_uint32),
+        ("reserved32", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint64 * 1),
     ]
 
 

@@ -126,6 +126,7 @@ struct Resolved {
   bool nosync, timing, use_graph, l2_persist, stats, sym, sel, stage;
   uint32_t wpg;
   bool lean;          // the 32-register instance of the plain / symmetric sweep
+  bool disperse;      // units handed out in dispersed runs
   uint64_t spin_limit, poison;
 };
 
@@ -157,6 +158,8 @@ mm_status resolve(const mm_graph* g, const mm_options* o, Resolved* r) {
   r->stage = o->stage_windows != 0;
   r->wpg = o->warps_per_graph;
   r->lean = sweep_lean(r->bits, r->block, r->blocks_per_sm);
+  if (o->unit_order > MM_ORDER_DISPERSED) return fail(MM_ERR_ARG, "unit_order must be 0, 1 or 2 (got %u)", o->unit_order);
+  r->disperse = o->unit_order == MM_ORDER_DISPERSED || (o->unit_order == MM_ORDER_AUTO && r->bits == 2);
   r->spin_limit = o->spin_limit ? o->spin_limit : kDefaultSpin;
   r->poison = o->poison_vertex;
   if (r->poison > g->n) return fail(MM_ERR_ARG, "poison_vertex out of range");
@@ -221,6 +224,7 @@ SweepParams make_params(mm_graph* g, const Resolved& r, uint32_t* d_mate) {
   P.tile = r.stage && !r.serial && !r.word && !g->host_mapped && aligned16;
   // the 32-register instance exists for the plain and symmetric sweeps only
   P.lean = r.lean && !r.serial && !r.stats && !P.sel && !P.tile;
+  P.disperse = r.disperse ? 1u : 0u;
   return P;
 }
 
@@ -835,6 +839,7 @@ BatchParams batch_params(mm_graph* g, const Resolved& r, uint64_t num_graphs, co
   B.P.work = work_ptr(g);
   B.P.err = err_ptr(g);
   B.P.spin_limit = r.spin_limit;
+  B.P.disperse = r.disperse ? 1u : 0u;
   B.vbase = d_vbase;
   B.ebase = d_ebase;
   B.num_graphs = num_graphs;
@@ -1165,6 +1170,7 @@ mm_status mm_autotune_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d
   for (uint32_t gr : grains)
     for (uint32_t sb : bits)
       for (int lean = 0; lean < 2; ++lean)
+        for (uint32_t ord : {MM_ORDER_ASCENDING, MM_ORDER_DISPERSED})
         for (uint32_t wg : wpgs) {
         // occupancy: the blocks per SM of the 40- or the 32-register instance
         const uint32_t bps = (uint32_t)sweep_blocks_per_sm((int)sb, (int)bt, lean != 0);
@@ -1173,6 +1179,7 @@ mm_status mm_autotune_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d
         c.status_bits = sb;
         c.block_threads = bt;
         c.blocks_per_sm = bps;
+        c.unit_order = ord;
         c.warps_per_graph = wg;
         c.serial = 0;
         c.use_graph = 0;
@@ -1206,6 +1213,7 @@ mm_status mm_autotune_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d
         best_o.status_bits = sb;
         best_o.block_threads = bt;
         best_o.blocks_per_sm = bps;
+        best_o.unit_order = ord;
         best_o.warps_per_graph = wg;
         }
   *o = best_o;

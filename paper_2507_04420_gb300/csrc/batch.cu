@@ -199,18 +199,21 @@ __global__ void __launch_bounds__(512, kLean ? 4 : 3) batch_sweep_kernel(BatchPa
   const unsigned lane = threadIdx.x & 31u;
   const uint64_t pol = policy_evict_first();
   const uint64_t units = B.totals[0];
+  const UnitOrder order(units, B.P.disperse != 0, (uint64_t)gridDim.x * (blockDim.x >> 5));
   for (;;) {
-    unsigned long long w = 0;
-    if (lane == 0) w = atomicAdd(B.P.work, 1ull);
-    w = __shfl_sync(kFull, w, 0);
-    if (w >= units) return;
+    unsigned long long c = 0;
+    if (lane == 0) c = atomicAdd(B.P.work, 1ull);
+    c = __shfl_sync(kFull, c, 0);
+    if (c >= order.total) return;
+    const uint64_t w = order.unit(c);
+    if (w >= units) continue;
     const uint32_t g = B.gid[w];
     const SweepParams P = graph_view<kLocal, kWord>(B, g);
     const int64_t row0 = B.part[2 * w];
     const int64_t e_begin = B.part[2 * w + 1];
     const int64_t e_end = (w + 1 < units && B.gid[w + 1] == g) ? B.part[2 * w + 3] : B.ebase[g + 1];
     if (e_begin < e_end) sweep_unit<S, false, kSym>(S(P), P, row0, e_begin, e_end, lane, pol);
-    if ((w & 15) == 0) {  // stop handing out work once an error is recorded
+    if ((c & 15) == 0) {  // stop handing out work once an error is recorded
       uint32_t e = 0;
       if (lane == 0) e = ld_relaxed(B.P.err);
       if (__shfl_sync(kFull, e, 0) & kErrTimeout) return;

@@ -83,6 +83,7 @@ extern "C" mm_status mm_skipper_static(uint64_t n, uint64_t nnz, const int64_t* 
     return reject(MM_ERR_UNSUPPORTED, "stats, stage_windows, symmetric and selective id loads need a handle "
                                       "(mm_create_csr)");
   if (o->id_loads > MM_ID_LOADS_SELECTIVE) return reject(MM_ERR_ARG, "id_loads must be 0, 1 or 2");
+  if (o->unit_order > MM_ORDER_DISPERSED) return reject(MM_ERR_ARG, "unit_order must be 0, 1 or 2");
   uint64_t grain = o->grain ? o->grain : 2048;
   if (grain % 128) return reject(MM_ERR_ARG, "grain must be a multiple of 128");
   const uint64_t items = n + nnz;
@@ -127,6 +128,7 @@ extern "C" mm_status mm_skipper_static(uint64_t n, uint64_t nnz, const int64_t* 
   P.units = (items + grain - 1) / grain;
   P.spin_limit = o->spin_limit ? o->spin_limit : (1ull << 20);
   P.poison = o->poison_vertex;
+  P.disperse = o->unit_order == MM_ORDER_DISPERSED ? 1u : 0u;   // byte states: ascending by default
 
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   if ((e = launch_prepare(P, 8, sms * 8, s, nullptr, 0)) != cudaSuccess) return cuda_fail("prepare launch", e);

@@ -63,6 +63,21 @@ struct SweepParams {
   // 1: the plain or symmetric instance compiled for 32 registers a thread
   // (64 warps per SM) instead of 40 (48 warps per SM)
   uint32_t lean;
+  // 1: work units handed out in dispersed runs (one run per warp of the grid)
+  uint32_t disperse;
+};
+
+// Unit order.  Counter value c is unit c (ascending), or, with dispersed
+// runs, unit (c mod R) * L + c / R for R runs of L units each, so that the
+// units in flight sit at evenly spaced positions and each run is walked in
+// order.  Counter values at or past `total` end the walk; values that map
+// past the last unit are skipped.
+struct UnitOrder {
+  uint64_t R, L, units, total;
+  __device__ UnitOrder(uint64_t units_, bool disperse, uint64_t runs)
+      : R(disperse ? runs : 1), L(disperse ? (units_ + runs - 1) / runs : units_), units(units_),
+        total(disperse ? R * L : units_) {}
+  __device__ __forceinline__ uint64_t unit(uint64_t c) const { return R == 1 ? c : (c % R) * L + c / R; }
 };
 
 // Sweep statistics, kept only by the kStats kernel instances.  A conflict is a

@@ -7,7 +7,8 @@
 //   stealing (Section IV-C).
 // sweep_kernel: Algorithm 1 lines 5-18.  Persistent warps take units from a
 //   global counter (the paper's idle threads steal work; here every unit is
-//   handed out on demand) and walk each with sweep_unit (walk.cuh): 32-row
+//   handed out on demand), in ascending order or in dispersed runs
+//   (UnitOrder, state.cuh), and walk each with sweep_unit (walk.cuh): 32-row
 //   windows whose row ends and row states are loaded in one step, matched
 //   rows skipped without a load, unmatched entries read 128 at a time with
 //   128-bit loads, filtered by the states of both endpoints, and the surviving
@@ -90,17 +91,20 @@ __global__ void __launch_bounds__(512, kLean ? 4 : 3) sweep_kernel(SweepParams P
   const uint64_t pol = policy_evict_first();
   uint32_t phase = 0;   // parity of the warp's tile barrier (kTile)
   if (kTile) init_window_tile(lane);
+  const UnitOrder order(P.units, P.disperse != 0, (uint64_t)gridDim.x * (blockDim.x >> 5));
   for (;;) {
-    unsigned long long w = 0;
-    if (lane == 0) w = atomicAdd(P.work, 1ull);
-    w = __shfl_sync(kFull, w, 0);
-    if (w >= P.units) return;
+    unsigned long long c = 0;
+    if (lane == 0) c = atomicAdd(P.work, 1ull);
+    c = __shfl_sync(kFull, c, 0);
+    if (c >= order.total) return;
+    const uint64_t w = order.unit(c);
+    if (w >= P.units) continue;
     const int64_t row0 = P.part[2 * w];
     const int64_t e_begin = P.part[2 * w + 1];
     const int64_t e_end = P.part[2 * w + 3];
     if (e_begin < e_end)
       sweep_unit<S, kStats, kSym, kSel, kTile>(s, P, row0, e_begin, e_end, lane, pol, &phase);
-    if ((w & 15) == 0) {  // stop handing out work once an error is recorded
+    if ((c & 15) == 0) {  // stop handing out work once an error is recorded
       uint32_t e = 0;
       if (lane == 0) e = ld_relaxed(P.err);
       if (__shfl_sync(kFull, e, 0) & kErrTimeout) return;

@@ -58,8 +58,9 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(mm_stats), offsetof(mm_stats, transitions),
          offsetof(mm_stats, illegal_transitions), offsetof(mm_stats, id_loads_open),
          offsetof(mm_options, id_loads), (size_t)MM_ID_LOADS_SELECTIVE);
-  printf("%zu %zu %zu %u\n", offsetof(mm_options, stage_windows), offsetof(mm_options, reserved),
-         offsetof(mm_options, warps_per_graph), MM_BATCH_LOCAL_IDS);
+  printf("%zu %zu %zu %u %zu %u\n", offsetof(mm_options, stage_windows), offsetof(mm_options, reserved),
+         offsetof(mm_options, warps_per_graph), MM_BATCH_LOCAL_IDS, offsetof(mm_options, unit_order),
+         MM_ORDER_DISPERSED);
   return 0;
 }
 """
@@ -78,7 +79,7 @@ int main(void) {
                     ctypes.sizeof(native.Stats), native.Stats.transitions.offset,
                     native.Stats.illegal_transitions.offset, native.Stats.id_loads_open.offset,
                     O.id_loads.offset, 2, O.stage_windows.offset, O.reserved.offset,
-                    O.warps_per_graph.offset, 4]
+                    O.warps_per_graph.offset, 4, O.unit_order.offset, 2]
 
 
 def test_default_options_and_argument_errors(native):

@@ -92,9 +92,9 @@ def test_parallel_local_ids_valid_per_graph(skp, batch, bits, use_graph, wpg):
     d = packed.csr.to("cuda")
     vb, eb = packed.vbase.cuda(), packed.ebase.cuda()
     with skp.Graph(d.offsets, d.nbrs, check=False, local_ids=True) as h:
-        for grain in (128, 1024):
+        for grain, order in ((128, 1), (1024, 2), (128, 0)):
             mate, gp = h.batched(vb, eb, graph_pairs=True, status_bits=bits, use_graph=use_graph,
-                                 warps_per_graph=wpg, grain=grain)
+                                 warps_per_graph=wpg, grain=grain, unit_order=order)
             m = _np(mate)
             u, per = _union_oracle(graphs, packed, m, local=True)
             assert u["flags"] == 0, u
@@ -111,9 +111,9 @@ def test_global_ids_with_a_warp_cap(skp, batch, wpg):
     vb, eb = packed.vbase.cuda(), packed.ebase.cuda()
     off, nb = packed.csr.offsets.numpy(), packed.csr.nbrs.numpy()
     with skp.Graph(d.offsets, d.nbrs) as h:
-        for bits in (2, 8, 32):
+        for bits, order in ((2, 0), (8, 2), (32, 1)):
             mate, gp = h.batched(vb, eb, graph_pairs=True, status_bits=bits, warps_per_graph=wpg,
-                                 grain=128, use_graph=1)
+                                 grain=128, use_graph=1, unit_order=order)
             m = _np(mate)
             vr = oracle.check(off, nb, m)
             vd = h.validate(mate)

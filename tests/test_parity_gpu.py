@@ -120,15 +120,26 @@ def test_launch_shapes(skp, bits, block):
 
 @pytest.mark.parametrize("bits", [2, 8, 32])
 @pytest.mark.parametrize("symmetric", [0, 1])
-def test_both_register_budgets(skp, bits, symmetric):
+def test_both_register_budgets_and_unit_orders(skp, bits, symmetric):
     """The plain and symmetric sweeps in their 40- and 32-register instances
-    (blocks_per_sm 3 and 4 of 512 threads; 0 = the layout's default), on a
-    power-law graph and on a grid, all with the oracle's verdict."""
-    for csr in (gg.rmat(14, 16, seed=12), gg.grid(200, 300)):
+    (blocks_per_sm 3 and 4 of 512 threads; 0 = the layout's default) and in
+    both unit orders (ascending, dispersed runs; 0 = the layout's default), on
+    a power-law graph, a grid and a graph whose units outnumber the warps
+    several times over, all with the oracle's verdict."""
+    for csr in (gg.rmat(14, 16, seed=12), gg.grid(200, 300), gg.erdos_renyi(300_000, 1_200_000, seed=13)):
         for bps in (0, 3, 4):
-            m, p, vr, vd = run(skp, csr, status_bits=bits, block_threads=512, blocks_per_sm=bps,
-                               symmetric=symmetric)
-            assert_parity(vr, vd)
+            for order in (0, 1, 2):
+                m, p, vr, vd = run(skp, csr, status_bits=bits, block_threads=512, blocks_per_sm=bps,
+                                   symmetric=symmetric, unit_order=order, grain=128)
+                assert_parity(vr, vd)
+
+
+def test_unit_order_out_of_range_is_refused(skp):
+    d = gg.grid(8, 8).to("cuda")
+    with skp.Graph(d.offsets, d.nbrs) as h:
+        with pytest.raises(skp.SkipperError) as e:
+            h.skipper(unit_order=3)
+        assert e.value.code == 1
 
 
 def _manual(n, rows):
