@@ -563,6 +563,27 @@ def run_side_graphs(args, skp, m_headline):
                                  "step_bytes_alg": step_bytes,
                                  "step_frac": step_bytes / (ms * 1e-3) / 1e9 / peak},
                     "verdict": {"flags": v.flags, "n_pairs": v.n_pairs}}
+            # the library's single-graph autotuner on this graph, then the same timing
+            t0 = time.time()
+            o_at = h.autotune()
+            at_s = time.time() - t0
+            o_at.nosync, o_at.timing = 1, 1
+            ms, sweep_ms, init_ms = time_sweep(h, mate, o_at, args.side_steps, args.warmup)
+            v = h.validate(mate)
+            if v.flags != 0:
+                raise SystemExit(f"invalid matching on {name} (autotuned): {v.as_dict()}")
+            achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9
+            res["layouts"]["autotuned"] = {
+                "ms_per_step": ms, "sweep_ms": sweep_ms, "init_ms": init_ms,
+                "value": g.nnz / (ms * 1e-3) / 1e9, "unit": UNIT,
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": None, "bytes_per_launch": sweep_bytes,
+                             "peak_kind": f"{peak_kind} hbm_gbs (burst copy)"},
+                "verdict": {"flags": v.flags, "n_pairs": v.n_pairs},
+                "settings": {"status_bits": o_at.status_bits, "grain": o_at.grain,
+                             "blocks_per_sm": o_at.blocks_per_sm,
+                             "unit_order": {1: "ascending", 2: "dispersed"}.get(o_at.unit_order, "auto"),
+                             "autotune_seconds": at_s}}
             h.skipper(mate=mate, status_bits=8, grain=args.grain, block_threads=args.block, stats=1)
             st = h.stats()
             res["stats_u8"] = {k: st[k] for k in ("entries_read", "windows", "chunks", "attempts", "matches",

@@ -439,6 +439,24 @@ mm_status mm_get_timing(mm_graph *g, mm_timing *out);
 mm_status mm_timing_history(mm_graph *g, mm_timing *out, uint32_t max, uint32_t *count);
 
 /*
+ * Autotuner for mm_skipper on one handle: times the candidate settings --
+ * grain in {2048, 8192}, status_bits in {2, 8, 32}, block_threads 512 with
+ * blocks_per_sm either the 40-register or the 32-register instance's
+ * occupancy, unit_order ascending or dispersed (edge-list handles: grain and
+ * status_bits only) -- on this graph with CUDA events: one untimed and three
+ * timed runs each, a candidate whose first timed run is already 1.5x slower
+ * than the best run so far being dropped.  Every new best is checked by
+ * mm_validate (an invalid result fails the call with MM_ERR_CUDA), and the
+ * fastest is written into *o; other fields of *o (symmetric, id_loads, ...)
+ * are kept and apply to every candidate.  d_mate_scratch: uint32_t[n].
+ * Synchronous.  No paper counterpart (the paper has no tuning parameters;
+ * the GPU's state width, occupancy and unit order are this library's).
+ * Errors: MM_ERR_ARG, MM_ERR_UNSUPPORTED (a MM_BATCH_LOCAL_IDS handle), and
+ * those of mm_skipper.
+ */
+mm_status mm_autotune(mm_graph *g, uint32_t *d_mate_scratch, mm_options *o, void *cuda_stream);
+
+/*
  * Autotuner for mm_skipper_batched: times the candidate settings -- grain in
  * {1024, 2048, 4096, 8192}, status_bits in {2, 8, 32}, block_threads 512 with
  * blocks_per_sm either the 40-register instance's or the 32-register

@@ -172,6 +172,13 @@ class Graph:
                                        ctypes.byref(v), _stream_ptr(stream)), "mm_validate_batched")
         return v
 
+    def autotune(self, stream=None, opts: Optional[Options] = None, **kw) -> Options:
+        """Fastest checked settings for skipper() on this graph (mm_autotune)."""
+        o = opts if opts is not None else options(**kw)
+        scratch = torch.empty(max(self.n, 1), dtype=torch.int32, device=self.device)
+        _check(lib.mm_autotune(self._h, _ptr(scratch), ctypes.byref(o), _stream_ptr(stream)), "mm_autotune")
+        return o
+
     def autotune_batched(self, vbase: torch.Tensor, ebase: torch.Tensor, stream=None,
                          opts: Optional[Options] = None, **kw) -> Options:
         o = opts if opts is not None else options(**kw)

@@ -204,6 +204,7 @@ SYMBOLS = [
     ("mm_get_stats", _I, [_P, ctypes.POINTER(Stats), _P]),
     ("mm_get_timing", _I, [_P, ctypes.POINTER(Timing)]),
     ("mm_timing_history", _I, [_P, ctypes.POINTER(Timing), _U32, ctypes.POINTER(_U32)]),
+    ("mm_autotune", _I, [_P, _P, ctypes.POINTER(Options), _P]),
     ("mm_autotune_batched", _I, [_P, _U64, _P, _P, _P, ctypes.POINTER(Options), _P]),
     ("mm_multi_create", _I, [ctypes.POINTER(_P)]),
     ("mm_skipper_multi", _I, [_P, _U64, ctypes.POINTER(GraphDesc), ctypes.POINTER(Options), _P]),

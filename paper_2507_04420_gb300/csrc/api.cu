@@ -1152,6 +1152,67 @@ mm_status mm_validate_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d
   return MM_OK;
 }
 
+mm_status mm_autotune(mm_graph* g, uint32_t* d_mate_scratch, mm_options* o, void* cuda_stream) {
+  g_err[0] = 0;
+  mm_status st = check_handle(g);
+  if (st != MM_OK) return st;
+  if (!o || (!d_mate_scratch && g->n)) return fail(MM_ERR_ARG, "null options or scratch");
+  if (g->local_ids) return fail(MM_ERR_UNSUPPORTED, "a MM_BATCH_LOCAL_IDS handle is tuned by mm_autotune_batched");
+  static const uint32_t grains[] = {2048, 8192};
+  static const uint32_t bits[] = {2, 8, 32};
+  const uint32_t bt = 512;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  float best = 1e30f;
+  mm_options best_o = *o;
+  for (uint32_t gr : grains)
+    for (uint32_t sb : bits)
+      for (int lean = 0; lean < 2; ++lean)
+        for (uint32_t ord : {MM_ORDER_ASCENDING, MM_ORDER_DISPERSED}) {
+          if (g->coo && (lean || ord == MM_ORDER_DISPERSED)) continue;  // edge lists: one instance, one order
+          const uint32_t bps = g->coo ? 0u : (uint32_t)sweep_blocks_per_sm((int)sb, (int)bt, lean != 0);
+          mm_options c = *o;
+          c.grain = gr;
+          c.status_bits = sb;
+          c.block_threads = bt;
+          c.blocks_per_sm = bps;
+          c.unit_order = ord;
+          c.serial = 0;
+          c.nosync = 0;
+          c.stats = 0;
+          c.timing = 1;
+          // one untimed run, then timed runs; dropped once 1.5x slower than the best run so far
+          float total = 0;
+          int reps = 0;
+          bool dropped = false;
+          for (int rep = 0; rep < 4; ++rep) {
+            if ((st = mm_skipper(g, &c, d_mate_scratch, nullptr, 0, nullptr, cuda_stream)) != MM_OK) return st;
+            mm_timing t;
+            if ((st = mm_get_timing(g, &t)) != MM_OK) return st;
+            if (rep == 0) continue;
+            total += t.total_ms;
+            ++reps;
+            if (rep == 1 && best < 1e30f && t.total_ms > 1.5f * (best / 3.0f)) {
+              dropped = true;
+              break;
+            }
+          }
+          if (dropped || reps != 3 || total >= best) continue;
+          mm_verdict v;
+          if ((st = mm_validate(g, d_mate_scratch, nullptr, 0, &v, cuda_stream)) != MM_OK) return st;
+          if (v.flags) return fail(MM_ERR_CUDA, "autotune candidate gave an invalid matching (flags 0x%x)", v.flags);
+          best = total;
+          best_o = *o;
+          best_o.grain = gr;
+          best_o.status_bits = sb;
+          best_o.block_threads = bt;
+          best_o.blocks_per_sm = bps;
+          best_o.unit_order = ord;
+        }
+  (void)s;
+  *o = best_o;
+  return MM_OK;
+}
+
 mm_status mm_autotune_batched(mm_graph* g, uint64_t num_graphs, const int64_t* d_vbase,
                               const int64_t* d_ebase, uint32_t* d_mate_scratch, mm_options* o,
                               void* cuda_stream) {

@@ -134,6 +134,27 @@ def test_both_register_budgets_and_unit_orders(skp, bits, symmetric):
                 assert_parity(vr, vd)
 
 
+def test_single_graph_autotuner(skp):
+    """mm_autotune picks checked settings; the picked settings give the
+    oracle's verdict on a power-law graph, a grid and an edge list."""
+    for csr in (gg.rmat(14, 16, seed=14), gg.grid(300, 300)):
+        off, nb = csr.offsets.numpy(), csr.nbrs.numpy()
+        d = csr.to("cuda")
+        with skp.Graph(d.offsets, d.nbrs) as h:
+            o = h.autotune()
+            assert o.status_bits in (2, 8, 32) and o.grain in (2048, 8192) and o.unit_order in (1, 2)
+            mate = h.skipper(opts=o)
+            vr = oracle.check(off, nb, _np(mate))
+            assert vr.flags == 0 and h.validate(mate).as_dict() == vr.as_dict()
+    csr = gg.rmat(12, 8, seed=15)
+    src, dst = gg.edge_list(csr, "shuffle", seed=3)
+    with skp.EdgeList(csr.n, src.cuda(), dst.cuda()) as h:
+        o = h.autotune()
+        mate = h.skipper(opts=o)
+        vr = oracle.check_edges(csr.n, src.numpy(), dst.numpy(), _np(mate))
+        assert vr.flags == 0 and h.validate(mate).as_dict() == vr.as_dict()
+
+
 def test_unit_order_out_of_range_is_refused(skp):
     d = gg.grid(8, 8).to("cuda")
     with skp.Graph(d.offsets, d.nbrs) as h:
