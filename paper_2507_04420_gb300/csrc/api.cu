@@ -1161,7 +1161,6 @@ mm_status mm_autotune(mm_graph* g, uint32_t* d_mate_scratch, mm_options* o, void
   static const uint32_t grains[] = {2048, 8192};
   static const uint32_t bits[] = {2, 8, 32};
   const uint32_t bt = 512;
-  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   float best = 1e30f;
   mm_options best_o = *o;
   for (uint32_t gr : grains)
@@ -1208,7 +1207,6 @@ mm_status mm_autotune(mm_graph* g, uint32_t* d_mate_scratch, mm_options* o, void
           best_o.blocks_per_sm = bps;
           best_o.unit_order = ord;
         }
-  (void)s;
   *o = best_o;
   return MM_OK;
 }
