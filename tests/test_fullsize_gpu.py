@@ -170,18 +170,21 @@ def c4_batch():
 
 @pytest.mark.parametrize("bits", [8, 2])
 def test_batched_4096_graphs_in_the_benchmark_launch(skp, c4_batch, bits):
-    """One CUDA-graph replay over the whole batch: the union and every member
-    graph (rebased to local ids) are checked by the oracle; the device's
+    """CUDA-graph replays over the whole batch (dispersed and ascending units):
+    the union and every member graph (rebased to local ids) are checked by the
+    oracle, the batch checker agrees with the union checker, and the device's
     per-graph pair counts equal the oracle's."""
     packed, off, nb, vb, eb, sgmm_pairs = c4_batch
     csr = packed.csr
     with skp.Graph(csr.offsets, csr.nbrs, check=False) as h:
         for rep in range(2):     # the second replay reuses the captured graph
             mate, gp = h.batched(packed.vbase, packed.ebase, graph_pairs=True, use_graph=1,
-                                 status_bits=bits, grain=8192, block_threads=512)
+                                 status_bits=bits, grain=8192, block_threads=512,
+                                 unit_order=2 - rep)   # dispersed, then ascending
             v = h.validate(mate)
             m = mate.cpu().numpy().view(np.uint32)
             _oracle_agrees(off, nb, m, v, sgmm_pairs)
+            assert h.validate_batched(packed.vbase, packed.ebase, mate).as_dict() == v.as_dict()
     gp = gp.cpu().numpy()
     G = vb.size - 1
     for k in range(G):
