@@ -85,16 +85,19 @@ typedef struct mm_options {
     uint32_t block_threads;  /* sweep threads per block, multiple of 32, <= 512;
                                 0 = 512 */
     uint32_t blocks_per_sm;  /* sweep blocks per SM; 0 = the occupancy maximum of the
-                                instance the layout uses by default.  The plain and
-                                symmetric CSR sweeps (single graph and batched) come
-                                in two instances: compiled for 40 registers a thread
-                                (3 blocks of 512 threads, 48 warps per SM; the
-                                default for 8- and 32-bit states) and for 32 (4
-                                blocks of 512, 64 warps per SM; the default for
-                                2-bit states, whose array stays in L2, so more
-                                warps hide more latency).  A value above what the
-                                40-register instance fits selects the 32-register
-                                one. */
+                                instance used by default.  The plain and symmetric
+                                CSR sweeps (single graph and batched) come in two
+                                instances: compiled for 40 registers a thread (3
+                                blocks of 512 threads, 48 warps per SM) and for 32
+                                (4 blocks of 512, 64 warps per SM).  By default the
+                                32-register one runs when the state array (the
+                                packed states, or the mate array in the 32-bit
+                                layout) takes at most half of the device's L2: it
+                                then stays in L2, and more warps hide more
+                                latency; a larger array's random sectors already
+                                load the memory system, and more warps only queue
+                                on it.  A value above what the 40-register instance
+                                fits selects the 32-register one. */
     uint32_t nosync;         /* 1: return without waiting for the GPU; the status
                                 of the work (timeout, bad id) is read by mm_sync() */
     uint32_t timing;         /* 1: record CUDA events around each kernel on the
@@ -170,7 +173,8 @@ typedef struct mm_options {
                                 open (uniform, grids) and cut the waits on ids
                                 with locality; the single band keeps the memory
                                 traffic of concurrent units close together.
-                                MM_ORDER_AUTO (0): dispersed for 2-bit states,
+                                MM_ORDER_AUTO (0): dispersed when the state array
+                                takes at most half of the L2 (see blocks_per_sm),
                                 ascending otherwise.  Other values: MM_ERR_ARG. */
     uint32_t reserved32;
     uint64_t reserved[1];
@@ -543,8 +547,9 @@ mm_status mm_destroy(mm_graph *g);
  * the reason in mm_last_error()); the grain is raised when needed so that the
  * partition fits the fixed table.  Options: status_bits 0 or 8, serial, grain,
  * block_threads, blocks_per_sm, spin_limit, poison_vertex, id_loads AUTO or
- * EAGER, unit_order (ascending unless MM_ORDER_DISPERSED).  The options that need a handle's own memory -- timing, use_graph,
- * nosync, l2_persist, stats, stage_windows, symmetric and id_loads SELECTIVE
+ * EAGER, unit_order; blocks_per_sm 0 and MM_ORDER_AUTO follow mm_options'
+ * rule for the byte state array.  The options that need a handle's own
+ * memory -- timing, use_graph, nosync, l2_persist, stats, stage_windows, symmetric and id_loads SELECTIVE
  * -- give MM_ERR_UNSUPPORTED; nothing is ignored silently.  The call waits for
  * its work and returns MM_OK, MM_ERR_TIMEOUT, MM_ERR_BAD_GRAPH, MM_ERR_ARG,
  * MM_ERR_UNSUPPORTED or MM_ERR_CUDA, with the reason of every failure in

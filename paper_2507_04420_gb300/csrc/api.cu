@@ -65,6 +65,7 @@ void skp::set_error_message(const char* fmt, ...) {
 struct mm_graph {
   int device = 0;
   int num_sms = 0;
+  int l2_bytes = 0;                   // the device's L2 size
   uint64_t n = 0, nnz = 0;            // nnz: stored entries (CSR) or listed edges (edge list)
   bool coo = false;                   // made by mm_create_coo: an edge list, no CSR
   bool host_mapped = false;           // the input arrays are host memory read in place
@@ -157,9 +158,13 @@ mm_status resolve(const mm_graph* g, const mm_options* o, Resolved* r) {
   r->sel = o->id_loads == MM_ID_LOADS_SELECTIVE || (o->id_loads == MM_ID_LOADS_AUTO && g->host_mapped);
   r->stage = o->stage_windows != 0;
   r->wpg = o->warps_per_graph;
-  r->lean = sweep_lean(r->bits, r->block, r->blocks_per_sm);
+  // defaults by the state array's size: at most half the L2 -> 64 warps per
+  // SM and dispersed units; larger -> 48 warps per SM and ascending units
+  const uint64_t state_bytes = r->word ? 4 * g->n : 4 * packed_words(g->n, r->bits);
+  const bool fits = g->l2_bytes > 0 && 2 * state_bytes <= (uint64_t)g->l2_bytes;
+  r->lean = sweep_lean(r->bits, r->block, r->blocks_per_sm, fits);
   if (o->unit_order > MM_ORDER_DISPERSED) return fail(MM_ERR_ARG, "unit_order must be 0, 1 or 2 (got %u)", o->unit_order);
-  r->disperse = o->unit_order == MM_ORDER_DISPERSED || (o->unit_order == MM_ORDER_AUTO && r->bits == 2);
+  r->disperse = o->unit_order == MM_ORDER_DISPERSED || (o->unit_order == MM_ORDER_AUTO && fits);
   r->spin_limit = o->spin_limit ? o->spin_limit : kDefaultSpin;
   r->poison = o->poison_vertex;
   if (r->poison > g->n) return fail(MM_ERR_ARG, "poison_vertex out of range");
@@ -365,6 +370,9 @@ mm_status new_handle(uint64_t n, uint64_t items, cudaStream_t s, mm_graph** out)
   mm_status st;
   if ((st = step(cudaGetDevice(&g->device), "cudaGetDevice")) != MM_OK) return st;
   if ((st = step(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device),
+                 "cudaDeviceGetAttribute")) != MM_OK)
+    return st;
+  if ((st = step(cudaDeviceGetAttribute(&g->l2_bytes, cudaDevAttrL2CacheSize, g->device),
                  "cudaDeviceGetAttribute")) != MM_OK)
     return st;
   g->n = n;

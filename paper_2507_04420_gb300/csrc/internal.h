@@ -12,9 +12,10 @@ namespace skp {
 // 32-register (lean = true) instance fits
 int sweep_blocks_per_sm(int bits, int block_threads, bool lean);
 // which instance a parallel CSR sweep uses: the 32-register one when the caller
-// asks for more blocks per SM than the default fits, or by default for 2-bit
-// states (their array stays in L2, so more warps hide more latency)
-bool sweep_lean(int bits, int block_threads, int blocks_per_sm);
+// asks for more blocks per SM than the default fits, or by default when the
+// state array takes at most half the L2 (it then stays there, and more warps
+// hide more latency; a larger array's random sectors already load the memory)
+bool sweep_lean(int bits, int block_threads, int blocks_per_sm, bool state_fits_l2);
 cudaError_t launch_prepare(const SweepParams& P, int bits, int grid, cudaStream_t s,
                            uint64_t* graph_pairs_zero, uint64_t num_graphs);
 cudaError_t launch_sweep(const SweepParams& P, int bits, int grid, int block, cudaStream_t s);

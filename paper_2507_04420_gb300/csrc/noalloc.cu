@@ -113,6 +113,12 @@ extern "C" mm_status mm_skipper_static(uint64_t n, uint64_t nnz, const int64_t* 
   int sms = 0;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return cuda_fail("cudaDeviceGetAttribute", e);
+  int l2 = 0;
+  if ((e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev)) != cudaSuccess)
+    return cuda_fail("cudaDeviceGetAttribute", e);
+  // byte states: 64 warps per SM and dispersed units by default when the state
+  // array takes at most half the L2, as in mm_skipper
+  const bool fits = l2 > 0 && 2 * (4 * packed_words(n, 8)) <= (uint64_t)l2;
 
   SweepParams P{};
   P.n = n;
@@ -128,14 +134,14 @@ extern "C" mm_status mm_skipper_static(uint64_t n, uint64_t nnz, const int64_t* 
   P.units = (items + grain - 1) / grain;
   P.spin_limit = o->spin_limit ? o->spin_limit : (1ull << 20);
   P.poison = o->poison_vertex;
-  P.disperse = o->unit_order == MM_ORDER_DISPERSED ? 1u : 0u;   // byte states: ascending by default
+  P.disperse = (o->unit_order == MM_ORDER_DISPERSED || (o->unit_order == MM_ORDER_AUTO && fits)) ? 1u : 0u;
 
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   if ((e = launch_prepare(P, 8, sms * 8, s, nullptr, 0)) != cudaSuccess) return cuda_fail("prepare launch", e);
   if (o->serial) {
     e = launch_serial(P, 8, s);
   } else {
-    P.lean = sweep_lean(8, block, (int)o->blocks_per_sm) ? 1u : 0u;
+    P.lean = sweep_lean(8, block, (int)o->blocks_per_sm, fits) ? 1u : 0u;
     const int per_sm = o->blocks_per_sm ? (int)o->blocks_per_sm : sweep_blocks_per_sm(8, block, P.lean != 0);
     e = launch_sweep(P, 8, sms * per_sm, block, s);
   }

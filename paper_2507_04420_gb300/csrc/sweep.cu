@@ -175,9 +175,9 @@ int sweep_blocks_per_sm(int bits, int block_threads, bool lean) {
   return b;
 }
 
-bool sweep_lean(int bits, int block_threads, int blocks_per_sm) {
+bool sweep_lean(int bits, int block_threads, int blocks_per_sm, bool state_fits_l2) {
   if (blocks_per_sm > 0) return blocks_per_sm > sweep_blocks_per_sm(bits, block_threads, false);
-  return bits == 2;
+  return state_fits_l2;
 }
 
 cudaError_t launch_prepare(const SweepParams& P, int bits, int grid, cudaStream_t s,
