@@ -94,7 +94,7 @@ __device__ __forceinline__ void init_window_tile(unsigned lane) {
   __syncwarp();
 }
 
-// One work unit: entries [pos, e_end), the first of which lies in row >= row0.
+// One work unit: entries [e_begin, e_end), the first of which lies in row >= row0.
 //
 // The warp keeps a window of 32 consecutive rows: lane k holds the end offset
 // of row wbase+k and the word holding that row vertex's state, both loaded in
@@ -116,13 +116,25 @@ __device__ __forceinline__ void init_window_tile(unsigned lane) {
 // where the bytes cross the host link.
 template <class S, bool kStats = false, bool kSym = false, bool kSel = false, bool kTile = false>
 __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int64_t row0,
-                                           int64_t pos, const int64_t e_end, const unsigned lane,
-                                           const uint64_t pol_stream, uint32_t* phase = nullptr) {
+                                           const int64_t e_begin, const int64_t e_end,
+                                           const unsigned lane, const uint64_t pol_stream,
+                                           uint32_t* phase = nullptr) {
   const uint32_t n32 = (uint32_t)P.n;
+  // Positions are entry indices relative to e_begin (a unit holds at most
+  // 2^24 items, so 32 bits suffice).  Row ends are clamped to [0, ue]: a row
+  // that ends before the unit reads as ending at 0, one that ends after it as
+  // ending at ue, which changes no comparison the walk makes.
+  const int ue = (int)(e_end - e_begin);
+  const int align = (int)(e_begin & 3);     // base of a chunk: ((pos + align) & ~3) - align
+  auto rel_end = [&](int64_t end) -> int {
+    const int64_t d = end - e_begin;
+    return d < 0 ? 0 : (d > (int64_t)ue ? ue : (int)d);
+  };
   int64_t wbase = row0;
-  int64_t my_end;
+  int my_end;
   uint32_t my_st;
   unsigned mchd;
+  int pos = 0;
   bool pending = false;                         // a copy of the next window's tile is in flight
   auto tile = [&]() { return &g_window_tiles[threadIdx.x >> 5]; };
   auto t_s = [&](int64_t w) { return (w + 1) & ~(int64_t)1; };
@@ -155,17 +167,17 @@ __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int
   {
     const int64_t r = wbase + lane;
     const bool in = r < (int64_t)P.n;
-    my_end = in ? __ldg(P.offsets + r + 1) : INT64_MAX;
+    my_end = in ? rel_end(__ldg(P.offsets + r + 1)) : ue;
     my_st = in ? s.peek((uint32_t)r) : 0u;
     mchd = __ballot_sync(kFull, !in || S::matched(my_st, (uint32_t)r));  // rows past n hold no entries
     issue_next(wbase + 32);
   }
-  while (pos < e_end) {
+  while (pos < ue) {
     // rows of the window with entries at or after pos that are not known matched
     const unsigned open = __ballot_sync(kFull, my_end > pos) & ~mchd;
     if (open == 0u) {  // the window is exhausted: continue after its last row
-      const int64_t win_end = __shfl_sync(kFull, my_end, 31);
-      if (win_end >= e_end) break;
+      const int win_end = __shfl_sync(kFull, my_end, 31);
+      if (win_end >= ue) break;
       if (win_end > pos) pos = win_end;
       wbase += 32;
       const int64_t r = wbase + lane;
@@ -180,11 +192,11 @@ __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int
         }
       }
       if (from_tile) {
-        my_end = in ? tile()->ends[wbase + 1 + lane - t_s(wbase)] : INT64_MAX;
+        my_end = in ? rel_end(tile()->ends[wbase + 1 + lane - t_s(wbase)]) : ue;
         my_st = in ? tile()->st[(r / (int64_t)S::kPerWord) - t_sw(wbase)] : 0u;
         __syncwarp();
       } else {
-        my_end = in ? __ldg(P.offsets + r + 1) : INT64_MAX;
+        my_end = in ? rel_end(__ldg(P.offsets + r + 1)) : ue;
         my_st = in ? s.peek((uint32_t)r) : 0u;
       }
       mchd = __ballot_sync(kFull, !in || S::matched(my_st, (uint32_t)r));
@@ -194,32 +206,33 @@ __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int
     }
     const int k1 = __ffs(open) - 1;
     if (k1 > 0) {  // row k1 starts where row k1-1 ends
-      const int64_t st = __shfl_sync(kFull, my_end, k1 - 1);
+      const int st = __shfl_sync(kFull, my_end, k1 - 1);
       if (st > pos) pos = st;
     }
-    if (pos >= e_end) break;
-    const int64_t win_end = __shfl_sync(kFull, my_end, 31);
-    const int64_t base = pos & ~(int64_t)3;
-    int64_t cend = base + 128;
-    if (cend > e_end) cend = e_end;
+    if (pos >= ue) break;
+    const int win_end = __shfl_sync(kFull, my_end, 31);
+    const int base = ((pos + align) & ~3) - align;
+    int cend = base + 128;
+    if (cend > ue) cend = ue;
     if (cend > win_end) cend = win_end;
-    // chunk-relative 32-bit coordinates: entry base+p, p in [lo_r, hi_r)
-    const int lo_r = (int)(pos - base);
-    const int hi_r = (int)(cend - base);
+    // chunk-relative coordinates: entry base+p, p in [lo_r, hi_r)
+    const int lo_r = pos - base;
+    const int hi_r = cend - base;
     if (kStats && lane == 0) {
       atomicAdd(P.stats + kStChunks, 1ull);
       atomicAdd(P.stats + kStEntries, (unsigned long long)(hi_r - lo_r));
     }
-    const int64_t rel64 = my_end - base;
-    const int rel = rel64 < 0 ? -1 : (rel64 > 129 ? 129 : (int)rel64);
+    int rel = my_end - base;
+    rel = rel < 0 ? -1 : (rel > 129 ? 129 : rel);
 
     // neighbour ids (one aligned 128-bit load per lane) and, in parallel, a
     // fresh read of the head row's state
     const int p0 = 4 * (int)lane;
-    const int64_t e0 = base + p0;
+    const int64_t e0 = e_begin + base + p0;
     uint32_t y[4] = {0u, 0u, 0u, 0u};
     if (!kSel && p0 < hi_r) load_quad(P, e0, pol_stream, y);
-    const uint32_t x1 = (uint32_t)(wbase + k1);
+    const uint32_t wb32 = (uint32_t)wbase;
+    const uint32_t x1 = wb32 + (uint32_t)k1;
     uint32_t head = 0;
     if (lane == 0) head = s.peek(x1);  // consumed after the row search, so both loads overlap it
 
@@ -239,7 +252,7 @@ __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int
     if (lane == (unsigned)k1) my_st = head;
     uint32_t xs[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) xs[j] = (uint32_t)(wbase + k[j]);
+    for (int j = 0; j < 4; ++j) xs[j] = wb32 + (uint32_t)k[j];
     if (kSel || kStats) {
       // does this lane's quad hold an entry of a row not known matched?
       bool open_quad = false;
@@ -290,14 +303,14 @@ __device__ __forceinline__ void sweep_unit(const S& s, const SweepParams& P, int
       if (!__any_sync(kFull, have)) break;
       const int j = have ? __ffs(cand) - 1 : 0;
       const uint32_t key = have ? pick4(xs, j) : kNone;
-      const uint32_t rxj = __shfl_sync(kFull, my_st, (key - (uint32_t)wbase) & 31);
+      const uint32_t rxj = __shfl_sync(kFull, my_st, (key - wb32) & 31);
       const unsigned peers = __match_any_sync(kFull, key);
       const int leader = __ffs(peers) - 1;
       unsigned done = 0u;
       if (have && (int)lane == leader) {
         cand &= ~(1u << j);
         if (resolve_edge<S, kStats>(s, key, pick4(y, j), rxj, pick4(ry, j), P))
-          done = 1u << (key - (uint32_t)wbase);
+          done = 1u << (key - wb32);
       }
       done = __reduce_or_sync(kFull, done);  // rows that are now matched
       mchd |= done;
