@@ -80,8 +80,13 @@ typedef struct mm_options {
     uint32_t serial;         /* 1: one GPU thread walks rows in ascending order and
                                 neighbours in stored order (per graph in batched
                                 mode); the result equals sequential greedy MM. */
-    uint32_t grain;          /* merge-path items (rows + entries) per work unit;
-                                0 = 2048.  Must be a multiple of 128 when set. */
+    uint32_t grain;          /* merge-path items (rows + entries; edges for an edge
+                                list) per work unit.  Must be a multiple of 128
+                                when set.  0 = chosen from the graph: about two
+                                units per resident sweep warp, the nearest power
+                                of two in [512, 8192] (up to 32768 for
+                                MM_HOST_MAPPED handles, whose units each start by
+                                waiting on the host link). */
     uint32_t block_threads;  /* sweep threads per block, multiple of 32, <= 512;
                                 0 = 512 */
     uint32_t blocks_per_sm;  /* sweep blocks per SM; 0 = the occupancy maximum of the
@@ -360,6 +365,35 @@ mm_status mm_host_device_address(const void *host, const void **device_out);
  */
 mm_status mm_skipper(mm_graph *g, const mm_options *o, uint32_t *d_mate, uint32_t *d_pairs,
                      uint64_t cap, uint64_t *d_count, void *cuda_stream);
+
+/*
+ * The same pass (Algorithm 1) with its result copied into host memory while
+ * it runs.  The merge-path units are taken in ascending order, in `pieces`
+ * consecutive launches of about equal unit counts; once a launch has ended,
+ * every row before the first row of the next unit has been walked to its end,
+ * so each of those vertices is MCHD or has only MCHD neighbours (Section
+ * II-B's maximality, row by row) and its mate can no longer change.  That
+ * prefix of d_mate is copied to h_mate on a second stream while the next
+ * launches run; the last copy follows the last launch.  No paper
+ * counterpart: it hides the device-to-host copy of the result behind the pass
+ * for callers whose results go to host memory.
+ *
+ *   d_mate   uint32_t[n] in device memory, caller-owned, written in full.
+ *   h_mate   uint32_t[n] in page-locked host memory, caller-owned, equal to
+ *            d_mate when the call has completed.
+ *   pieces   1..MM_MAX_PIECES launches (fewer when the graph has fewer units).
+ * o as for mm_skipper, with units in ascending order (MM_ORDER_AUTO is taken
+ * as ascending; MM_ORDER_DISPERSED, serial, stats, timing and use_graph give
+ * MM_ERR_UNSUPPORTED).  Edge-list and MM_BATCH_LOCAL_IDS handles:
+ * MM_ERR_UNSUPPORTED.  Errors: MM_ERR_ARG (null arrays with n > 0, pieces out
+ * of range, h_mate not page-locked host memory), MM_ERR_TIMEOUT,
+ * MM_ERR_BAD_GRAPH, MM_ERR_CUDA.  Waits for the GPU (after one short wait
+ * for the prepare step, whose partition sets the copies' sizes) unless
+ * o->nosync, in which case mm_sync or a wait on the stream ends the call.
+ */
+#define MM_MAX_PIECES 64u
+mm_status mm_skipper_to_host(mm_graph *g, const mm_options *o, uint32_t *d_mate, uint32_t *h_mate,
+                             uint32_t pieces, void *cuda_stream);
 
 /*
  * Batched Skipper over num_graphs graphs packed block-diagonally in the

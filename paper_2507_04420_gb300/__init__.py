@@ -145,6 +145,24 @@ class Graph:
             return mate, d_pairs, d_count
         return mate
 
+    def skipper_to_host(self, host_mate: torch.Tensor, mate: Optional[torch.Tensor] = None,
+                        pieces: int = 8, stream=None, opts: Optional[Options] = None, **kw) -> torch.Tensor:
+        """Run Skipper with the result copied into `host_mate` (page-locked,
+        int32[n]) piece by piece while the pass runs (mm_skipper_to_host);
+        `mate` is the device array it is computed in.  Returns host_mate."""
+        o = opts if opts is not None else options(**kw)
+        if mate is None:
+            mate = torch.empty(self.n, dtype=torch.int32, device=self.device)
+        _need(mate, "mate", _U32)
+        if mate.numel() != self.n or host_mate.numel() != self.n:
+            raise ValueError("mate and host_mate must have n entries")
+        if host_mate.dtype not in _U32 or host_mate.is_cuda or not host_mate.is_contiguous():
+            raise ValueError("host_mate must be a contiguous int32 host tensor")
+        _check(lib.mm_skipper_to_host(self._h, ctypes.byref(o), _ptr(mate), ctypes.c_void_p(host_mate.data_ptr()),
+                                      pieces, _stream_ptr(stream)),
+               "mm_skipper_to_host")
+        return host_mate
+
     def batched(self, vbase: torch.Tensor, ebase: torch.Tensor, mate: Optional[torch.Tensor] = None,
                 graph_pairs: bool = False, stream=None, opts: Optional[Options] = None, **kw):
         """Batched Skipper over a block-diagonal packing (vbase/ebase int64[G+1] on device)."""
@@ -396,14 +414,18 @@ class HostSession:
     (pageable tensors, zero_copy=False, or check=True, whose checker reads
     every entry and is better served by one bulk copy): the CSR is copied into
     device buffers kept for up to (n_max, nnz_max).  Either way the mate array
-    is computed in device memory and copied back."""
+    is computed in device memory and copied back; read in place, it comes
+    back in `pieces` parts while the pass runs (mm_skipper_to_host), unless
+    the options ask for what that call does not run (dispersed units, serial
+    mode, statistics, timing, a CUDA graph)."""
 
     HANDLES = 16   # handles kept per way in (least recently used first out)
 
-    def __init__(self, n_max: int, nnz_max: int, device=None, zero_copy: bool = True):
+    def __init__(self, n_max: int, nnz_max: int, device=None, zero_copy: bool = True, pieces: int = 3):
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.n_max, self.nnz_max = n_max, nnz_max
         self.zero_copy = zero_copy
+        self.pieces = pieces
         self.dev = dev
         self.d_off = self.d_nb = None       # copy-path buffers, made on first use
         self.d_mate = torch.empty(max(n_max, 1), dtype=torch.int32, device=dev)
@@ -411,6 +433,7 @@ class HostSession:
         self._mapped = collections.OrderedDict()   # host-mapped handles, keyed by the host arrays
         self.last_verdict = None
         self.last_mode = None
+        self.last_pieces = 0   # > 0: the last run copied its result back in pieces
 
     def run(self, offsets: torch.Tensor, nbrs: torch.Tensor, mate_out: Optional[torch.Tensor] = None,
             stream=None, check: bool = False, **kw) -> torch.Tensor:
@@ -423,6 +446,7 @@ class HostSession:
             return self._run(offsets, nbrs, mate_out, stream, check, n, nnz, mate_d, **kw)
 
     def _run(self, offsets, nbrs, mate_out, stream, check, n, nnz, mate_d, **kw):
+        self.last_pieces = 0
         if self.zero_copy and not check and offsets.is_pinned() and (nnz == 0 or nbrs.is_pinned()):
             self.last_mode = "host_mapped"
             key = (offsets.data_ptr(), nbrs.data_ptr(), n, nnz)
@@ -433,6 +457,17 @@ class HostSession:
                 while len(self._mapped) > self.HANDLES:
                     self._mapped.popitem(last=False)[1].close()
             self._mapped.move_to_end(key)
+            o = kw.get("opts") or options(**{k: v for k, v in kw.items() if k != "opts"})
+            if (self.pieces and o.unit_order != 2 and not o.serial and not o.stats and not o.timing
+                    and not o.use_graph):
+                if mate_out is None:
+                    mate_out = torch.empty(n, dtype=torch.int32, pin_memory=True)
+                if mate_out.is_pinned():
+                    self.last_pieces = self.pieces
+                    self.last_verdict = None
+                    g.skipper_to_host(mate_out, mate=mate_d, pieces=self.pieces, stream=stream, opts=o)
+                    (stream or torch.cuda.current_stream()).synchronize()
+                    return mate_out
         else:
             self.last_mode = "copy"
             if self.d_off is None:

@@ -197,6 +197,7 @@ SYMBOLS = [
     ("mm_host_device_address", _I, [_P, ctypes.POINTER(_P)]),
     ("mm_state_census", _I, [_P, ctypes.POINTER(_U64), _P]),
     ("mm_skipper", _I, [_P, ctypes.POINTER(Options), _P, _P, _U64, _P, _P]),
+    ("mm_skipper_to_host", _I, [_P, ctypes.POINTER(Options), _P, _P, _U32, _P]),
     ("mm_skipper_batched", _I, [_P, _U64, _P, _P, ctypes.POINTER(Options), _P, _P, _P]),
     ("mm_validate", _I, [_P, _P, _P, _U64, ctypes.POINTER(Verdict), _P]),
     ("mm_validate_batched", _I, [_P, _U64, _P, _P, _P, ctypes.POINTER(Verdict), _P]),

@@ -36,7 +36,7 @@ mm_status fail(mm_status st, const char* fmt, ...) {
                   #expr, cudaGetErrorString(e_), __func__);                                  \
   } while (0)
 
-constexpr uint32_t kDefaultGrain = 2048;
+constexpr uint32_t kDefaultGrain = 2048;   // partition table sized at creation for this grain
 constexpr int kDefaultBlock = 512;
 constexpr uint64_t kDefaultSpin = 1ull << 20;
 
@@ -108,6 +108,12 @@ struct mm_graph {
   int64_t* bpart = nullptr;
   uint64_t bunits_cap = 0;
   BatchGraph bg2;                     // the CUDA graph of these launches
+  // mm_skipper_to_host: the stream of the copies back, one event per launch,
+  // pinned unit starts [0, MM_MAX_PIECES] and row splits after them
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t piece_ev[MM_MAX_PIECES + 1] = {};
+  cudaEvent_t pieces_done = nullptr;  // the last call's work, so its pinned reads are over
+  uint64_t* h_split = nullptr;
 };
 
 namespace {
@@ -141,7 +147,7 @@ mm_status resolve(const mm_graph* g, const mm_options* o, Resolved* r) {
   r->bits = (int)bits;
   r->word = bits == 32;
   r->serial = o->serial != 0;
-  r->grain = o->grain ? o->grain : kDefaultGrain;
+  r->grain = o->grain;
   if (r->grain % 128 || r->grain > (1u << 24))
     return fail(MM_ERR_ARG, "grain must be a multiple of 128 and at most 2^24 (got %u)", r->grain);
   r->block = o->block_threads ? (int)o->block_threads : kDefaultBlock;
@@ -165,6 +171,19 @@ mm_status resolve(const mm_graph* g, const mm_options* o, Resolved* r) {
   r->lean = sweep_lean(r->bits, r->block, r->blocks_per_sm, fits);
   if (o->unit_order > MM_ORDER_DISPERSED) return fail(MM_ERR_ARG, "unit_order must be 0, 1 or 2 (got %u)", o->unit_order);
   r->disperse = o->unit_order == MM_ORDER_DISPERSED || (o->unit_order == MM_ORDER_AUTO && fits);
+  // grain 0: about two units per resident warp, the nearest power of two in
+  // [512, 8192] -- small graphs need many units to occupy the GPU, large ones
+  // lose to per-unit set-up below 4096; over the host link, where every
+  // unit's first window waits on the link, up to 32768
+  if (r->grain == 0) {
+    const uint64_t items = g->coo ? g->nnz : g->n + g->nnz;
+    const uint64_t warps = (uint64_t)(g->num_sms > 0 ? g->num_sms : 1) * (r->lean ? 64u : 48u);
+    const uint64_t target = items / (2 * warps);
+    const uint32_t cap = g->host_mapped ? 32768u : 8192u;
+    uint32_t grain = 512;
+    while (grain < cap && (uint64_t)grain * 1414 < target * 1000) grain *= 2;
+    r->grain = grain;
+  }
   r->spin_limit = o->spin_limit ? o->spin_limit : kDefaultSpin;
   r->poison = o->poison_vertex;
   if (r->poison > g->n) return fail(MM_ERR_ARG, "poison_vertex out of range");
@@ -296,6 +315,15 @@ struct L2Window {
     return MM_OK;
   }
 };
+
+mm_status ensure_pieces(mm_graph* g) {
+  if (g->h_split) return MM_OK;
+  CUDA_TRY(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking));
+  for (auto& e : g->piece_ev) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreateWithFlags(&g->pieces_done, cudaEventDisableTiming));
+  CUDA_TRY(cudaHostAlloc(&g->h_split, 2 * (MM_MAX_PIECES + 1) * sizeof(uint64_t), cudaHostAllocDefault));
+  return MM_OK;
+}
 
 mm_status ensure_hist(mm_graph* g) {
   if (g->hist_ready) return MM_OK;
@@ -489,7 +517,7 @@ mm_status mm_default_options(mm_options* o) {
   if (!o) return fail(MM_ERR_ARG, "null options");
   memset(o, 0, sizeof *o);
   o->status_bits = 8;
-  o->grain = kDefaultGrain;
+  o->grain = 0;
   o->block_threads = kDefaultBlock;
   o->spin_limit = kDefaultSpin;
   return MM_OK;
@@ -638,6 +666,80 @@ mm_status mm_skipper(mm_graph* g, const mm_options* o, uint32_t* d_mate, uint32_
   }
   if (ev) CUDA_TRY(cudaEventRecord(ev[3], s));
   CUDA_TRY(cudaMemcpyAsync(g->h_err, err_ptr(g), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  if (r.nosync) return MM_OK;
+  return read_err(g, s);
+}
+
+mm_status mm_skipper_to_host(mm_graph* g, const mm_options* o, uint32_t* d_mate, uint32_t* h_mate,
+                             uint32_t pieces, void* cuda_stream) {
+  g_err[0] = 0;
+  mm_status st = check_handle(g);
+  if (st != MM_OK) return st;
+  if (g->local_ids) return fail(MM_ERR_UNSUPPORTED, "a MM_BATCH_LOCAL_IDS handle runs batched calls only");
+  if (g->coo) return fail(MM_ERR_UNSUPPORTED, "an edge list has no rows to finish in order");
+  if (g->n && (!d_mate || !h_mate)) return fail(MM_ERR_ARG, "null mate");
+  if (pieces < 1 || pieces > MM_MAX_PIECES)
+    return fail(MM_ERR_ARG, "pieces must be 1..%u (got %u)", MM_MAX_PIECES, pieces);
+  if (o && o->unit_order == MM_ORDER_DISPERSED)
+    return fail(MM_ERR_UNSUPPORTED, "the launches take units in ascending order");
+  Resolved r;
+  if ((st = resolve(g, o, &r)) != MM_OK) return st;
+  if (r.serial || r.stats || r.timing || r.use_graph)
+    return fail(MM_ERR_UNSUPPORTED, "serial, stats, timing and use_graph are not available here");
+  r.disperse = false;
+  if (g->n) {
+    cudaPointerAttributes a{};
+    CUDA_TRY(cudaPointerGetAttributes(&a, h_mate));
+    if (a.type != cudaMemoryTypeHost) return fail(MM_ERR_ARG, "h_mate must be page-locked host memory");
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const uint64_t units = (g->n + g->nnz + r.grain - 1) / r.grain;
+  if ((st = ensure_part(g, units)) != MM_OK) return st;
+  if ((st = ensure_pieces(g)) != MM_OK) return st;
+  CUDA_TRY(cudaEventSynchronize(g->pieces_done));   // a call left running on another stream
+  SweepParams P = make_params(g, r, d_mate);
+  g->stats_valid = false;
+  g->last_bits = r.bits;
+  g->last_state = P.state;
+  CUDA_TRY(launch_prepare(P, r.bits, prepare_grid_for(g, units), s, nullptr, 0));
+  const uint64_t K = units == 0 ? 0 : (pieces < units ? pieces : units);
+  // launch i takes units [i*units/K, (i+1)*units/K); after it, every row
+  // before part[2 * (i+1)*units/K] (the first row of the next unit) is done
+  uint64_t* hU = g->h_split;
+  uint64_t* hR = g->h_split + (MM_MAX_PIECES + 1);
+  for (uint64_t i = 1; i < K; ++i)
+    CUDA_TRY(cudaMemcpyAsync(hR + i, g->part + 2 * (i * units / K), sizeof(uint64_t),
+                             cudaMemcpyDeviceToHost, s));
+  // the split rows size the copies; this also ends the previous call's reads of hU
+  CUDA_TRY(cudaStreamSynchronize(s));
+  for (uint64_t i = 0; i < K; ++i) hU[i] = i * units / K;
+  L2Window win;
+  if ((st = win.open(g, r, s, P.state, r.word ? g->n * 4 : packed_words(g->n, r.bits) * 4)) != MM_OK) return st;
+  const int grid = sweep_grid_for(g, r, P.lean != 0, units);
+  uint64_t done_rows = 0;
+  for (uint64_t i = 0; i < K; ++i) {
+    if (i > 0)   // the unit counter starts at this launch's first unit
+      CUDA_TRY(cudaMemcpyAsync(work_ptr(g), hU + i, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+    SweepParams Pi = P;
+    Pi.units = (i + 1) * units / K;
+    CUDA_TRY(launch_sweep(Pi, r.bits, grid, r.block, s));
+    const uint64_t rows = i + 1 == K ? g->n : (hR[i + 1] < g->n ? hR[i + 1] : g->n);
+    if (rows > done_rows) {
+      CUDA_TRY(cudaEventRecord(g->piece_ev[i], s));
+      CUDA_TRY(cudaStreamWaitEvent(g->copy_stream, g->piece_ev[i], 0));
+      CUDA_TRY(cudaMemcpyAsync(h_mate + done_rows, d_mate + done_rows, (rows - done_rows) * sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, g->copy_stream));
+      done_rows = rows;
+    }
+  }
+  if ((st = win.close()) != MM_OK) return st;
+  if (g->n > done_rows)   // no units (a graph of isolated vertices): the prepared mate
+    CUDA_TRY(cudaMemcpyAsync(h_mate + done_rows, d_mate + done_rows, (g->n - done_rows) * sizeof(uint32_t),
+                             cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaEventRecord(g->piece_ev[MM_MAX_PIECES], g->copy_stream));
+  CUDA_TRY(cudaStreamWaitEvent(s, g->piece_ev[MM_MAX_PIECES], 0));
+  CUDA_TRY(cudaMemcpyAsync(g->h_err, err_ptr(g), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaEventRecord(g->pieces_done, s));
   if (r.nosync) return MM_OK;
   return read_err(g, s);
 }
@@ -1311,6 +1413,11 @@ mm_status mm_destroy(mm_graph* g) {
   if (g->tile_counts) cudaFree(g->tile_counts);
   if (g->h_err) cudaFreeHost(g->h_err);
   if (g->h_counters) cudaFreeHost(g->h_counters);
+  for (auto& e : g->piece_ev)
+    if (e) cudaEventDestroy(e);
+  if (g->pieces_done) cudaEventDestroy(g->pieces_done);
+  if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
+  if (g->h_split) cudaFreeHost(g->h_split);
   delete g;
   return MM_OK;
 }

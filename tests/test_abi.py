@@ -86,7 +86,7 @@ def test_default_options_and_argument_errors(native):
     lib = native.load(native.LIB_PATH)
     o = native.Options()
     assert lib.mm_default_options(ctypes.byref(o)) == 0
-    assert (o.status_bits, o.grain, o.block_threads, o.spin_limit) == (8, 2048, 512, 1 << 20)
+    assert (o.status_bits, o.grain, o.block_threads, o.spin_limit) == (8, 0, 512, 1 << 20)   # grain 0: by size
     assert lib.mm_default_options(None) == 1
     assert b"null" in lib.mm_last_error()
     # argument checks happen before any device work

@@ -115,8 +115,8 @@ def test_csr_rmat27_read_in_place_from_host_memory(skp, rmat27, rmat27_host):
     h_off, h_nb, off, nb, sgmm_pairs = rmat27_host
     sess = skp.HostSession(g.n, g.nnz)
     try:
-        m_host = sess.run(h_off, h_nb, **BENCH_OPTS)
-        assert sess.last_mode == "host_mapped"
+        m_host = sess.run(h_off, h_nb, status_bits=8)          # the benchmark's e2e line: grain by size
+        assert sess.last_mode == "host_mapped" and sess.last_pieces == 3   # copied back in pieces
         with skp.Graph(g.offsets, g.nbrs, check=False) as h:
             v = h.validate(m_host.cuda())
         m = m_host.numpy().view(np.uint32)
