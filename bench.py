@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--e2e-grain", type=int, default=0,
                     help="grain of the end-to-end runs; 0 = the library's choice for the handle "
                          "(larger units for a CSR read in place over the host link)")
-    ap.add_argument("--e2e-pieces", type=int, default=3,
+    ap.add_argument("--e2e-pieces", type=int, default=0,
                     help="launches whose finished mate prefixes are copied back while the pass runs "
                          "(mm_skipper_to_host); 0 = one launch, then one copy")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -985,10 +985,10 @@ def run_ours(args):
                "h2d_bytes_per_step": read_bytes, "d2h_bytes_per_step": 4 * n, "mode": zc_mode,
                "how": "HostSession.run on pinned host tensors: the kernels read the CSR in place "
                       "(MM_HOST_MAPPED, selective id loads) -- h2d bytes = all row ends + the id "
-                      "quads loaded (stats counter); mm_skipper_to_host: the pass in ascending "
-                      "launches, each finished prefix of the mate copied to pinned host memory "
-                      "while the next launches run (mm_skipper then one copy with "
-                      "--e2e-pieces 0); sync",
+                      "quads loaded (stats counter); grain by the library (larger units over the "
+                      "host link); mm_skipper, then the mate -> pinned host in one copy (with "
+                      "--e2e-pieces K: mm_skipper_to_host, K ascending launches, each finished "
+                      "prefix of the mate copied back while the next ones run); sync",
                "copy_path": {"value": job_gedges(world, nnz, cp_s), "unit": UNIT, "ms_per_step": cp_s * 1e3,
                              "h2d_bytes_per_step": 8 * (n + 1) + 4 * nnz, "d2h_bytes_per_step": 4 * n,
                              "mode": cp_mode,

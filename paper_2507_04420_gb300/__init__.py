@@ -414,14 +414,14 @@ class HostSession:
     (pageable tensors, zero_copy=False, or check=True, whose checker reads
     every entry and is better served by one bulk copy): the CSR is copied into
     device buffers kept for up to (n_max, nnz_max).  Either way the mate array
-    is computed in device memory and copied back; read in place, it comes
-    back in `pieces` parts while the pass runs (mm_skipper_to_host), unless
-    the options ask for what that call does not run (dispersed units, serial
-    mode, statistics, timing, a CUDA graph)."""
+    is computed in device memory and copied back; read in place with
+    pieces > 0, it comes back in that many parts while the pass runs
+    (mm_skipper_to_host), unless the options ask for what that call does not
+    run (dispersed units, serial mode, statistics, timing, a CUDA graph)."""
 
     HANDLES = 16   # handles kept per way in (least recently used first out)
 
-    def __init__(self, n_max: int, nnz_max: int, device=None, zero_copy: bool = True, pieces: int = 3):
+    def __init__(self, n_max: int, nnz_max: int, device=None, zero_copy: bool = True, pieces: int = 0):
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.n_max, self.nnz_max = n_max, nnz_max
         self.zero_copy = zero_copy
