@@ -86,7 +86,8 @@ typedef struct mm_options {
                                 units per resident sweep warp, the nearest power
                                 of two in [512, 8192] (up to 32768 for
                                 MM_HOST_MAPPED handles, whose units each start by
-                                waiting on the host link). */
+                                waiting on the host link).  mm_skipper_multi and
+                                mm_skipper_static take 0 as 2048. */
     uint32_t block_threads;  /* sweep threads per block, multiple of 32, <= 512;
                                 0 = 512 */
     uint32_t blocks_per_sm;  /* sweep blocks per SM; 0 = the occupancy maximum of the
