@@ -59,7 +59,8 @@ struct Req {
 
 struct Tick {
   int slot = 0;
-  std::vector<Req> reqs;
+  std::vector<Req> reqs;          // with their device buffers, released once the tick is done
+  uint32_t* arena = nullptr;      // mates of the in-place requests
   cudaEvent_t checked = nullptr, back = nullptr;
 };
 
@@ -152,6 +153,17 @@ void release_orphans(mm_server* s, std::vector<Req>& staged) {
 // Everything the worker holds fails with `st` (a worker failure).
 void fail_all(mm_server* s, std::deque<Req>& pending, std::vector<Req>& staged,
               std::deque<Tick>& inflight, mm_status st) {
+  for (Tick& t : inflight) {   // buffers of launched work: released once every stream is done
+    for (Req& r : t.reqs)
+      if (r.own) {
+        s->orphans.push_back(const_cast<int64_t*>(r.off));
+        s->orphans.push_back(const_cast<uint32_t*>(r.nb));
+        s->orphans.push_back(r.mate);
+        r.own = false;
+      }
+    if (t.arena) s->orphans.push_back(t.arena);
+    t.arena = nullptr;
+  }
   release_orphans(s, staged);
   for (Req& r : pending) finish(s, r, st, nullptr);
   for (Req& r : staged) finish(s, r, st, nullptr);
@@ -247,25 +259,16 @@ mm_status launch_tick(mm_server* s, std::vector<Req>& staged, std::deque<Tick>& 
     }
   }
   W_TRY(cudaEventRecord(t.checked, st));
-  // results back to the callers' buffers once the pass is done; device buffers
-  // released once the checker has passed them too
+  // results back to the callers' buffers once the pass is done; the device
+  // buffers stay with the tick until complete() has seen its checker and
+  // these copies finish, and are then released on the copy stream, so the
+  // copies of later requests can reuse them without waiting on another stream
   W_TRY(cudaStreamWaitEvent(s->d2h, swept, 0));
   for (const Req& r : staged)
     if (r.n && r.h_mate)
       W_TRY(cudaMemcpyAsync(r.h_mate, r.mate, 4 * r.n, cudaMemcpyDeviceToHost, s->d2h));
   W_TRY(cudaEventRecord(t.back, s->d2h));
-  W_TRY(cudaStreamWaitEvent(s->d2h, t.checked, 0));
-  for (Req& r : staged)
-    if (r.own) {   // each pointer is dropped once its release is enqueued
-      W_TRY(cudaFreeAsync(const_cast<int64_t*>(r.off), s->d2h));
-      r.off = nullptr;
-      W_TRY(cudaFreeAsync(const_cast<uint32_t*>(r.nb), s->d2h));
-      r.nb = nullptr;
-      W_TRY(cudaFreeAsync(r.mate, s->d2h));
-      r.mate = nullptr;
-      r.own = false;
-    }
-  if (arena) W_TRY(cudaFreeAsync(arena, s->d2h));
+  t.arena = arena;
   *arena_out = nullptr;
   s->event_pool.push_back(copied);   // recorded work keeps the event; reuse is stream-ordered
   s->event_pool.push_back(swept);
@@ -302,6 +305,18 @@ mm_status complete(mm_server* s, Tick& t, bool* ready) {
       return vs;
     }
   }
+  for (Req& r : t.reqs)
+    if (r.own) {   // the tick's work on them is done: free on the copy stream
+      W_TRY(cudaFreeAsync(const_cast<int64_t*>(r.off), s->h2d));
+      r.off = nullptr;
+      W_TRY(cudaFreeAsync(const_cast<uint32_t*>(r.nb), s->h2d));
+      r.nb = nullptr;
+      W_TRY(cudaFreeAsync(r.mate, s->h2d));
+      r.mate = nullptr;
+      r.own = false;
+    }
+  if (t.arena) W_TRY(cudaFreeAsync(t.arena, s->h2d));
+  t.arena = nullptr;
   for (size_t i = 0; i < t.reqs.size(); ++i) {
     finish(s, t.reqs[i], pass, v.empty() ? nullptr : &v[i]);
     s->used -= t.reqs[i].bytes;
