@@ -581,6 +581,7 @@ mm_status mm_server_destroy(mm_server* s) {
   s->cv_work.notify_all();
   if (s->worker.joinable()) s->worker.join();   // drains every queued request
   const mm_status failure = s->failure;
+  if (s->h2d) cudaStreamSynchronize(s->h2d);   // the last launches' buffers are freed on it
   cudaStreamSynchronize(s->d2h);
   for (int i = 0; i < 2; ++i) {
     if (s->slot_stream[i]) cudaStreamSynchronize(s->slot_stream[i]);
