@@ -6,7 +6,9 @@
  * edges 01 02 03 12 23, stored as a symmetric CSR with ascending rows.
  * Serial mode must give sequential greedy matching's result, mate = 1 0 3 2;
  * the parallel pass must give a maximal matching the checker accepts; the
- * same edges as a list must do the same; two copies of the graph packed as a
+ * same edges as a list must do the same; the pass with its result copied to
+ * page-locked host memory while it runs must leave the host copy equal to
+ * the device result; two copies of the graph packed as a
  * batch with local ids must give that result in each copy, replayed from a
  * CUDA graph; and the native server must return the serial result for a
  * host-memory request.
@@ -64,6 +66,22 @@ int main(void)
         printf("parallel verdict flags %u pairs %llu\n", v.flags, (unsigned long long)v.n_pairs);
         return 1;
     }
+    uint32_t *h_mate = NULL;
+    if (cudaMallocHost((void **)&h_mate, sizeof mate) != cudaSuccess) {
+        printf("cudaMallocHost failed\n");
+        return 1;
+    }
+    if ((st = mm_skipper_to_host(g, &o, d_mate, h_mate, 2, NULL)) != MM_OK) return failed("mm_skipper_to_host", st);
+    cudaMemcpy(mate, d_mate, sizeof mate, cudaMemcpyDeviceToHost);
+    if (memcmp(mate, h_mate, sizeof mate) != 0) {
+        printf("host copy %u %u %u %u differs from the device result\n", h_mate[0], h_mate[1], h_mate[2], h_mate[3]);
+        return 1;
+    }
+    if ((st = mm_validate(g, d_mate, NULL, 0, &v, NULL)) != MM_OK || v.flags != 0 || v.n_pairs != 2)
+        return failed("mm_validate after mm_skipper_to_host", st);
+    if ((st = mm_skipper_to_host(g, &o, d_mate, mate, 2, NULL)) != MM_ERR_ARG)   /* pageable: refused */
+        return failed("mm_skipper_to_host into pageable memory (expected MM_ERR_ARG)", st);
+    cudaFreeHost(h_mate);
     mm_destroy(g);
 
     /* the same edges as a list (each once, one reversed) */
