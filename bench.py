@@ -62,7 +62,7 @@ def parse():
                     help="mm_options.blocks_per_sm of the timed sweep (0 = the layout's default)")
     ap.add_argument("--stage-windows", action="store_true",
                     help="mm_options.stage_windows = 1 for the timed sweep (opt-in TMA window tiles)")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--e2e-grain", type=int, default=0,
                     help="grain of the end-to-end runs; 0 = the library's choice for the handle "
                          "(larger units for a CSR read in place over the host link)")
