@@ -65,6 +65,41 @@ def test_read_in_place_with_both_register_budgets(skp):
                 assert oracle.check(off, nb, hm.numpy().view(np.uint32)).flags == 0
 
 
+@pytest.mark.parametrize("kw", [dict(symmetric=1), dict(id_loads=2), dict(l2_persist=1),
+                                dict(status_bits=2, blocks_per_sm=3), dict(unit_order=1, grain=384)])
+def test_options_the_pass_keeps(skp, kw):
+    """Options that change how the sweep runs but not the ascending launches."""
+    for g in (gg.rmat(15, 16, seed=12), gg.grid(200, 257), gg.star(30_000)):
+        off, nb = g.offsets.numpy(), g.nbrs.numpy()
+        with skp.Graph(g.offsets.cuda(), g.nbrs.cuda()) as h:
+            hm = _pinned_empty(g.n)
+            dm = torch.empty(g.n, dtype=torch.int32, device="cuda")
+            h.skipper_to_host(hm, mate=dm, pieces=5, **kw)
+            assert torch.equal(hm, dm.cpu()), kw
+            assert oracle.check(off, nb, hm.numpy().view(np.uint32)).flags == 0, kw
+
+
+def test_a_packed_batch_with_global_ids(skp):
+    """A block-diagonal batch is one CSR to this call; every member graph's
+    part of the host copy is a maximal matching of that graph."""
+    packed, _ = gg.batch_packed(24, 1e3, 3e4, seed=13, device="cuda")
+    csr = packed.csr
+    with skp.Graph(csr.offsets, csr.nbrs) as h:
+        hm = _pinned_empty(csr.n)
+        dm = torch.empty(csr.n, dtype=torch.int32, device="cuda")
+        h.skipper_to_host(hm, mate=dm, pieces=7)
+        assert torch.equal(hm, dm.cpu())
+        assert h.validate_batched(packed.vbase, packed.ebase, dm).flags == 0
+    m = hm.numpy().view(np.uint32)
+    vb, eb = packed.vbase.cpu().numpy(), packed.ebase.cpu().numpy()
+    off, nb = csr.offsets.cpu().numpy(), csr.nbrs.cpu().numpy()
+    for k in range(len(vb) - 1):
+        v0, v1, e0, e1 = vb[k], vb[k + 1], eb[k], eb[k + 1]
+        sub = m[v0:v1].copy()
+        sub[sub != 0xFFFFFFFF] -= np.uint32(v0)
+        assert oracle.check(off[v0:v1 + 1] - e0, nb[e0:e1] - v0, sub).flags == 0, k
+
+
 def test_nosync_then_sync(skp):
     g = gg.rmat(13, 16, seed=9)
     with skp.Graph(g.offsets.cuda(), g.nbrs.cuda()) as h:
