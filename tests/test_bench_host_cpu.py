@@ -87,3 +87,15 @@ def test_every_global_name_bench_uses_is_defined():
             local.add(node.name)
     missing = sorted(used - defined - local)
     assert not missing, missing
+
+
+def test_batch_profile_name_matches_the_committed_summary():
+    class O:   # the batched autotuner's usual pick on the 4096-graph batch
+        grain, blocks_per_sm, unit_order, warps_per_graph = 8192, 4, 2, 0
+    name = bench.batch_profile_name(4096, O())
+    assert name == "c4batch4096_g8192_b4_dispersed_w0"
+    path = os.path.join(bench.ROOT, "profiles", f"sweep_u8_{name}.md")
+    text = open(path).read()
+    assert "kernel_source_sha256_16:" in text and "dram_bytes_per_launch:" in text
+    O.unit_order = 0
+    assert bench.batch_profile_name(4096, O()).endswith("_auto_w0")
