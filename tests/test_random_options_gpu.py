@@ -1,7 +1,8 @@
 """Seeded random graphs through random option settings, every result checked
 by the oracle (Section II-B's definition) and by the device checker with an
 identical verdict: state layout, register budget (blocks per SM), unit order
-(ascending or dispersed), grain, symmetric filter, and for batches global or
+(ascending or dispersed), grain (0: chosen by the library), symmetric filter,
+the result copied to host memory in pieces while the pass runs, and for batches global or
 local ids with a warps-per-graph cap, with and without the CUDA graph.  The
 graphs mix families and shapes the fixed tests do not pin: loops, unsorted
 rows, empty rows, isolated vertices and runs of consecutive ids."""
@@ -63,7 +64,7 @@ def _random_graph(rng):
 
 def _opts(rng):
     bits = int(rng.choice([2, 8, 32]))
-    return dict(status_bits=bits, grain=int(rng.choice([128, 256, 1024, 8192])),
+    return dict(status_bits=bits, grain=int(rng.choice([0, 128, 256, 1024, 8192])),
                 blocks_per_sm=int(rng.choice([0, 1, 3, 4])), unit_order=int(rng.integers(0, 3)),
                 block_threads=int(rng.choice([128, 256, 512])))
 
@@ -83,6 +84,12 @@ def test_random_graphs_and_options(skp):
             vr = oracle.check(off, nb, m)
             assert vr.flags == 0, (it, o, vr.as_dict())
             assert h.validate(mate).as_dict() == vr.as_dict(), (it, o)
+            if o["unit_order"] != 2:   # the pieces need ascending units
+                pieces = int(rng.integers(1, 9))
+                hm = torch.empty(g.n, dtype=torch.int32, pin_memory=True)
+                h.skipper_to_host(hm, mate=mate, pieces=pieces, **o)
+                assert torch.equal(hm, mate.cpu()), (it, o, pieces)
+                assert oracle.check(off, nb, hm.numpy().view(np.uint32)).flags == 0, (it, o, pieces)
 
 
 def test_random_batches_and_options(skp):
